@@ -1,0 +1,348 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test ties one step of the oracle to the paper's printed claim, a closed form, an
+invariant, a library routine or a brute-force computation, so that a dropped term, a wrong
+sign or index, or a transposed operand anywhere in the oracle fails at least one of them.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import p3m_synth as S
+from oracle import p3m_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+# ----------------------------------------------------------------- split convention
+
+
+def test_cutoff_claim_of_the_guide():
+    """Ch. Parameters, P3M_cutoff: cutoff >= 4.8 scale units leaves < 1 % of the force out."""
+    g = _golden("cutoff_claim.txt")
+    x = np.linspace(g["cutoff_in_scale"], 12.0, 2001)
+    assert np.all(O.g_split(x) < g["max_fraction_left_out"])
+    # and the claim is tight: just below 4.8 the fraction left out is not yet small
+    assert O.g_split(4.5) > g["max_fraction_left_out"]
+    assert O.g_split(4.8) > 0.5 * g["max_fraction_left_out"]
+
+
+def test_split_is_gaussian_cloud_mass_outside_r():
+    """The long-range filter exp(-k^2 r_s^2) is the transform of a Gaussian cloud
+    rho(r) ~ exp(-r^2 / (4 r_s^2)); the short-range force fraction g(r/r_s) must equal the
+    fraction of that cloud's mass outside radius r (Gauss's law), integrated numerically."""
+    rs = 1.0
+
+    def dens(r):
+        return r * r * math.exp(-r * r / (4.0 * rs * rs))
+
+    total = integrate.quad(dens, 0, np.inf, epsabs=1e-15, epsrel=1e-13)[0]
+    for x in [0.0, 0.3, 1.0, 2.0, 3.3, 4.5, 4.8, 7.0]:
+        outside = integrate.quad(dens, x * rs, np.inf, epsabs=1e-15, epsrel=1e-13)[0] / total
+        assert abs(O.g_split(x) - outside) < 1e-13
+
+
+# ----------------------------------------------------------------- Ewald oracle
+
+
+def test_ewald_single_particle_and_lattice_zero():
+    L, gm = 1.0, 1.0
+    one = np.array([[0.31], [0.77], [0.05]])
+    assert np.max(np.abs(O.ewald_accel(one, L, gm))) < 1e-13
+    q = S.lattice(4, L) + 0.1
+    a = O.ewald_accel(q, L, gm)
+    assert np.max(np.abs(a)) < 1e-11 * gm / (L / 4) ** 2
+
+
+def test_ewald_alpha_independent():
+    pos = S.uniform_random(40, 1.0, 7)
+    a1 = O.ewald_accel(pos, 1.0, 1.0, alpha=2.2)
+    a2 = O.ewald_accel(pos, 1.0, 1.0, alpha=3.1)
+    assert np.max(np.abs(a1 - a2)) < 1e-11 * np.max(np.abs(a1))
+
+
+@pytest.mark.parametrize("r", [0.01, 0.03, 0.05])
+def test_ewald_close_pair_closed_form(r):
+    """Periodic point mass with neutralising background, near the mass:
+    a = -Gm r_vec/r^3 + (4 pi/3) Gm r_vec / L^3 + O(r^3/L^5) (cubic symmetry)."""
+    L, gm = 1.0, 1.0
+    rng = S.uniform01(99, 6)
+    for t in range(2):
+        th, ph = math.acos(2 * rng[2 * t] - 1), 2 * math.pi * rng[2 * t + 1]
+        u = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        pos = np.stack([np.array([0.4, 0.5, 0.6]), np.array([0.4, 0.5, 0.6]) + r * u], axis=1)
+        a = O.ewald_accel(pos, L, gm)[:, 1]
+        expect = (-gm / r ** 2 + 4.0 * math.pi / 3.0 * gm * r / L ** 3) * u
+        assert np.linalg.norm(a - expect) < 40.0 * r ** 3 * gm / L ** 5 + 1e-12 * gm / r ** 2
+
+
+def test_split_independence_exact_ksum_plus_short_range_equals_ewald():
+    """Without the mesh (exact k-sum) and with a cutoff where g is negligible, the long- and
+    short-range parts together are the Ewald sum with alpha = 1/(2 r_s), for any r_s."""
+    L, n = 1.0, 48
+    pos = S.uniform_random(n, L, 3)
+    ref = O.ewald_accel(pos, L, O.Params(L, n, 64).gm)
+    for rs_cells, mesh in [(1.25, 32), (0.9, 40)]:
+        p = O.Params(L, n, mesh, r_s_cells=rs_cells, cutoff=12.0)
+        assert p.r_c < 0.5 * L
+        assert O.g_split(12.0) < 1e-14
+        kmax = int(math.ceil(6.5 / p.r_s * L / (2 * math.pi)))
+        lr = O.lr_accel_exact(pos, p, kmax=kmax)
+        sr, _ = O.sr_accel(pos, p, brute=True)
+        err = np.max(np.abs(lr + sr - ref)) / np.max(np.abs(ref))
+        assert err < 1e-10, (rs_cells, err)
+
+
+# ----------------------------------------------------------------- mesh (PM) part
+
+
+def test_zero_self_force():
+    p = O.Params(20.0, 1, 16)
+    for seed in range(3):
+        x = S.uniform_random(1, 20.0, seed)
+        a = O.pm_accel(x, p)
+        assert np.max(np.abs(a)) < 1e-14 * p.gm / p.h ** 2
+
+
+def test_perfect_lattice_has_no_force():
+    p = O.Params(32.0, 24 ** 3, 24, softening=0.0)
+    q = S.lattice(24, 32.0)
+    a = O.accel(q, p)
+    assert np.max(np.abs(a)) < 1e-12 * p.gm / p.h ** 2
+
+
+def test_momentum_conserved_by_pm_and_sr():
+    p = O.Params(50.0, 3000, 24, softening=0.02)
+    pos = S.uniform_random(3000, 50.0, 11)
+    lr = O.pm_accel(pos, p)
+    sr, _ = O.sr_accel(pos, p)
+    for a in (lr, sr):
+        assert np.max(np.abs(a.sum(axis=1))) < 1e-12 * np.abs(a).sum()
+
+
+def test_pm_matches_exact_ksum():
+    """Mesh long-range force (CIC + FFT + deconvolution) vs the mesh-free k-sum.  The
+    difference is the CIC aliasing of the mesh: under 2 % at r_s = 1.25 h, shrinking as r_s/h
+    grows, and larger without the W(k)^-2 deconvolution."""
+    L, n = 1.0, 200
+    pos = S.uniform_random(n, L, 5)
+    errs = {}
+    for rsc in (1.25, 3.0):
+        for dec in (True, False):
+            p = O.Params(L, n, 32, r_s_cells=rsc, deconvolve=dec)
+            kmax = int(math.ceil(6.5 / p.r_s * L / (2 * math.pi)))
+            ref = O.lr_accel_exact(pos, p, kmax=kmax)
+            pm = O.pm_accel(pos, p)
+            errs[rsc, dec] = np.sqrt(np.mean(np.sum((pm - ref) ** 2, 0))
+                                     / np.mean(np.sum(ref ** 2, 0)))
+    assert errs[1.25, True] < 2e-2, errs
+    assert errs[3.0, True] < 6e-3, errs
+    assert errs[1.25, True] < 0.5 * errs[1.25, False]
+    assert errs[3.0, True] < 0.5 * errs[3.0, False]
+
+
+@pytest.mark.parametrize("rs_cells,bias_tol,rms_tol", [(1.25, 1.2e-2, 2e-2), (2.5, 2e-3, 3e-3)])
+def test_p3m_two_body_is_newton_plus_ewald(rs_cells, bias_tol, rms_tol):
+    """Two particles 2h..L/8 apart along random directions: P3M pair force vs the Ewald pair
+    force.  The orientation-averaged bias and the rms are the mesh anisotropy; both shrink
+    when r_s grows from 1.25 h to 2.5 h (same r_c), as a discretisation error must."""
+    L, M = 64.0, 32
+    p = O.Params(L, 2, M, softening=0.0, r_s_cells=rs_cells, cutoff=4.5 * 1.25 / rs_cells)
+    h = L / M
+    u = S.uniform01(1234, 5 * 40)
+    ratios = []
+    for t in range(40):
+        r = 2.0 * h + u[5 * t] * (L / 8 - 2.0 * h)
+        th, ph = math.acos(2 * u[5 * t + 1] - 1), 2 * math.pi * u[5 * t + 2]
+        d = r * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        x0 = np.array([u[5 * t + 3], u[5 * t + 4], 0.5]) * L
+        pos = O.wrap(np.stack([x0, x0 + d], axis=1), L)
+        a = O.accel(pos, p)[:, 1]
+        ref = O.ewald_accel(pos, L, p.gm)[:, 1]
+        ratios.append(np.dot(a, ref) / np.dot(ref, ref))
+    ratios = np.array(ratios)
+    assert abs(np.mean(ratios) - 1.0) < bias_tol
+    assert np.sqrt(np.mean((ratios - 1.0) ** 2)) < rms_tol
+
+
+def test_p3m_vs_ewald_random_set():
+    L, n = 64.0, 512
+    pos = S.uniform_random(n, L, 21)
+    p = O.Params(L, n, 32, softening=0.0)
+    ref = O.ewald_accel(pos, L, p.gm)
+    a = O.accel(pos, p)
+    rel = np.sqrt(np.mean(np.sum((a - ref) ** 2, 0)) / np.mean(np.sum(ref ** 2, 0)))
+    assert rel < 2e-2, rel
+    p6 = O.Params(L, n, 32, cutoff=5.4, softening=0.0)  # larger cutoff: smaller truncation
+    a6 = O.accel(pos, p6)
+    rel6 = np.sqrt(np.mean(np.sum((a6 - ref) ** 2, 0)) / np.mean(np.sum(ref ** 2, 0)))
+    assert rel6 < rel
+
+
+# ----------------------------------------------------------------- short range
+
+
+def test_sr_cells_equal_brute_force():
+    L, n = 60.0, 2500
+    pos = O.wrap(np.concatenate([S.uniform_random(2000, L, 4),
+                                 S.uniform_random(500, 3.0, 5) + 58.5], axis=1), L)
+    p = O.Params(L, n, 40, softening=0.03)
+    a1, n1 = O.sr_accel(pos, p)
+    a2, n2 = O.sr_accel(pos, p, brute=True)
+    assert n1 == n2 and n1 > 0
+    assert np.max(np.abs(a1 - a2)) < 1e-12 * np.max(np.abs(a2))
+    tg = np.array([0, 17, 2100, 2499])
+    a3, _ = O.sr_accel(pos, p, targets=tg)
+    assert np.array_equal(a3, a1[:, tg])
+
+
+def test_sr_single_pair_direction_and_magnitude():
+    """A lone pair at r: attraction along the separation, magnitude Gm g(r/r_s) / r^2."""
+    L = 40.0
+    p = O.Params(L, 2, 32, softening=0.0)
+    r = 0.6 * p.r_c
+    pos = np.array([[10.0, 10.0 + r], [5.0, 5.0], [7.0, 7.0]])
+    a, npairs = O.sr_accel(pos, p)
+    assert npairs == 2
+    mag = p.gm * float(O.g_split(r / p.r_s)) / r ** 2
+    assert abs(a[0, 0] - mag) < 1e-14 * mag and abs(a[0, 1] + mag) < 1e-14 * mag
+    assert np.max(np.abs(a[1:])) == 0.0
+
+
+# ----------------------------------------------------------------- keys, order, CIC
+
+
+def test_wrap_edges():
+    L = 10.0
+    x = np.array([-1e-300, -L, L, 2 * L + 3.0, -3.5, np.nextafter(L, 0), 0.0])
+    w = O.wrap(x, L)
+    assert np.all(w >= 0) and np.all(w < L)
+    assert w[1] == 0.0 and w[2] == 0.0 and w[3] == 3.0 and w[4] == 6.5 and w[6] == 0.0
+
+
+def test_keys_brute_force():
+    L = 100.0
+    p = O.Params(L, 1, 64, sub_bits=2)  # r_c = 8.79 -> n_c = 11
+    assert p.n_c == 11
+    rng = S.uniform01(5, 3 * 300)
+    cells = (rng[:900].reshape(3, 300) * p.n_fine).astype(np.int64)
+    pos = (cells + 0.5) * (L / p.n_fine)
+    pos[:, 0] = [0.0, np.nextafter(L, 0), 50.0]  # edges: 0, L - ulp, mid
+    cell, key = O.cell_keys(pos, p)
+    for i in range(300):
+        f = [min(int(pos[d, i] * p.n_fine / L), p.n_fine - 1) for d in range(3)]
+        c = [fd >> 2 for fd in f]
+        s = [fd & 3 for fd in f]
+        code = 0
+        for t in range(2):
+            for d in range(3):
+                code |= ((s[d] >> t) & 1) << (3 * t + d)
+        assert cell[i] == (c[2] * 11 + c[1]) * 11 + c[0]
+        assert key[i] == (cell[i] << 6) | code
+
+
+def test_stable_order_and_cell_start_brute_force():
+    keys = (S.uniform01(8, 500) * 7).astype(np.int64)
+    order = O.stable_order(keys)
+    assert list(order) == sorted(range(500), key=lambda i: (keys[i], i))
+    st = O.cell_start(keys[order], 9)
+    for c in range(9):
+        assert st[c + 1] - st[c] == np.sum(keys == c)
+    assert st[0] == 0 and st[9] == 500
+
+
+def test_cic_deposit_brute_force():
+    L, M = 10.0, 5
+    p = O.Params(L, 30, M, short_range=False)
+    pos = S.uniform_random(30, L, 2)
+    pos[:, 0] = [2.0, 4.0, 6.0]  # exactly on node (1, 2, 3)
+    rho = O.cic_deposit(pos, p)
+    ref = np.zeros((M, M, M))
+    h = L / M
+    for i in range(30):
+        u = pos[:, i] / h
+        i0 = np.floor(u).astype(int)
+        f = u - i0
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    w = ((f[0] if dx else 1 - f[0]) * (f[1] if dy else 1 - f[1])
+                         * (f[2] if dz else 1 - f[2]))
+                    ref[(i0[0] + dx) % M, (i0[1] + dy) % M, (i0[2] + dz) % M] += w
+    assert np.max(np.abs(rho - ref)) < 1e-14
+    assert abs(rho.sum() - 30) < 1e-12
+    one = O.cic_deposit(pos[:, :1], p)
+    assert one[1, 2, 3] == 1.0 and one.sum() == 1.0
+
+
+# ----------------------------------------------------------------- integration
+
+
+def test_kick_drift_factors_vs_quadrature():
+    eds = O.Params(10.0, 1, 8, short_range=False)
+    lcdm = O.Params(10.0, 1, 8, short_range=False, omega_m=0.3, omega_lambda=0.7)
+    for p in (eds, lcdm):
+        for a1, a2 in [(0.02, 0.03), (0.5, 0.55), (0.9, 1.0)]:
+            k = integrate.quad(lambda a: 1.0 / (a * a * O.hubble(a, p)), a1, a2,
+                               epsabs=1e-15, epsrel=1e-13)[0]
+            d = integrate.quad(lambda a: 1.0 / (a ** 3 * O.hubble(a, p)), a1, a2,
+                               epsabs=1e-15, epsrel=1e-13)[0]
+            assert abs(O.kick_factor(a1, a2, p) - k) < 1e-13 * abs(k)
+            assert abs(O.drift_factor(a1, a2, p) - d) < 1e-13 * abs(d)
+    # EdS Hubble rate a^-3/2
+    assert abs(O.hubble(0.25, eds) - 8.0) < 1e-14
+
+
+@pytest.mark.parametrize("short_range", [False, True])
+def test_zeldovich_plane_wave_linear_growth(short_range):
+    """Single-mode plane wave in EdS: the exact solution is x = q + a psi, p = m a^(3/2) psi
+    (Zel'dovich; linear growth D = a).  10 log-spaced KDK steps a = 0.02 -> 0.1 with the
+    lattice half a mesh cell off the nodes and a final density contrast of 5 %.  The residual
+    (~0.6-0.9 % in position, 1.3-1.9 % in momentum) is the CIC discretisation, which grows with
+    the amplitude; a wrong G, Green's-function constant or kick/drift factor is off by O(1)."""
+    n, L = 24, 48.0
+    k = 2 * math.pi / L
+    a0, a1 = 0.02, 0.1
+    amp = 0.05 / (a1 * k)
+    q, pos, mom = S.plane_wave(n, L, a0, amp, offset_cells=0.5)
+    p = O.Params(L, n ** 3, n, softening=0.0, short_range=short_range)
+    acc = O.accel(pos, p)
+    a_s = S.log_spaced_steps(a0, a1, 10)
+    for i in range(10):
+        pos, mom, acc = O.step(pos, mom, acc, a_s[i], a_s[i + 1] - a_s[i], p)
+    psi = amp * np.sin(k * (q[0] - 0.5 * L / n))
+    dx = pos[0] - q[0]
+    dx -= L * np.round(dx / L)
+    err = np.max(np.abs(dx - a1 * psi)) / (a1 * amp)
+    assert err < 1.5e-2, err
+    assert np.max(np.abs(pos[1:] - O.wrap(q[1:], L))) < 1e-9 * L
+    perr = np.max(np.abs(mom[0] - a1 ** 1.5 * psi)) / (a1 ** 1.5 * amp)
+    assert perr < 3e-2, perr
+
+
+def test_momentum_constant_over_steps():
+    n, L = 16, 40.0
+    pos, mom = S.zeldovich(n, L, 0.05, 77, rms_cells=0.3)
+    p = O.Params(L, n ** 3, 20, softening=0.02)
+    acc = O.accel(pos, p)
+    p0 = O.momentum(mom)
+    scale = np.abs(mom).sum()
+    a_s = S.log_spaced_steps(0.05, 0.2, 5)
+    for i in range(5):
+        pos, mom, acc = O.step(pos, mom, acc, a_s[i], a_s[i + 1] - a_s[i], p)
+    assert np.max(np.abs(O.momentum(mom) - p0)) < 1e-12 * scale
