@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Throughput of the P3M gravity step on one GB300 (or N independent replicas).
+
+Workload (default): 128^3 particles, 128^3 mesh, box 200 Mpc/h, r_s = 1.25 mesh cells,
+cutoff 4.5 r_s, softening 0.02 mean spacings, Einstein-de Sitter, seeded Zel'dovich ICs
+(P(k) ~ k^-2 exp(-(k/k_c)^2), k_c = k_Nyq/2, rms displacement 0.2 cells at a = 0.02),
+evolved by the GPU path through 64 log-spaced steps a = 0.02 -> 1 to a clustered state
+(untimed set-up).  W warm-up and K timed kick-drift-kick steps then continue from a = 1 with
+the same logarithmic spacing.  One step = one pass of the whole hot path (kick/drift, keys,
+sort, permute, CIC deposit, FFT, k-space pass, 3 inverse FFTs, CIC gather, pair sum, kick).
+
+Printed: one JSON line (rank 0).  `value` = particle-updates/s of the whole job with the
+state resident in HBM; `e2e` = the same metric through the C ABI with host (pinned) buffers,
+host<->device copies of positions, momenta and accelerations inside the timed region.
+
+--impl reference runs the FP64 CPU oracle on the host cores instead (no GPU work): each
+step is the oracle's full mesh force at 128^3 plus its pair sum on a sample of particles of
+a synthetic clustered 128^3 snapshot, plus the kick/drift of all particles.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import p3m_synth as S  # noqa: E402
+
+METRIC = "P3M particle-updates/s"
+UNIT = "particle-updates/s"
+# algorithmic FP32 operations per accepted pair of the short-range sum (FMA = 2, each of
+# rsqrt/sqrt/exp/erfc = 1): d 3, r^2 5, +eps^2 1, 1/s 1, 1/s^3 2, r 1, x 1, g 8, f 1, a += 6
+FLOPS_PER_PAIR = 29
+WORKLOAD = dict(n_p=128, mesh=128, box=200.0, r_s_cells=1.25, cutoff=4.5, softening=0.02,
+                a_begin=0.02, a_end=1.0, setup_steps=64, seed=1512)
+WORKLOAD_NAME = ("clustered_128: 128^3 particles, 128^3 mesh, box 200 Mpc/h, r_s 1.25 cells, "
+                 "cutoff 4.5 r_s, softening 0.02, EdS; seeded Zel'dovich ICs evolved 64 log "
+                 "steps a=0.02->1 on the GPU, timed steps continue from a=1")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle timing (host)
+
+
+def oracle_step_time(pos, mom, n_sample, seed):
+    """Seconds the FP64 oracle needs for one step of this particle set: the full mesh force
+    (all particles), the pair sum on n_sample particles scaled to all N, and the kick/drift of
+    all particles.  Returns (seconds, threads, description)."""
+    from oracle import p3m_oracle as O
+    w = WORKLOAD
+    n = pos.shape[1]
+    p = O.Params(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"], w["softening"])
+    x = O.wrap(pos, w["box"])
+    t0 = time.perf_counter()
+    lr = O.pm_accel(x, p)
+    t1 = time.perf_counter()
+    tg = np.unique((S.uniform01(seed, n_sample) * n).astype(np.int64) % n)
+    O.sr_accel(x, p, targets=tg)
+    t2 = time.perf_counter()
+    m = mom + lr * O.kick_factor(1.0, 1.02, p)
+    x2 = O.wrap(x + m * O.drift_factor(1.0, 1.04, p), w["box"])
+    del x2
+    t3 = time.perf_counter()
+    total = (t1 - t0) + (t2 - t1) * n / tg.size + (t3 - t2)
+    desc = (f"full mesh force and kick/drift for all {n} particles; short-range pair sum for "
+            f"{tg.size} sampled particles, scaled by {n / tg.size:.1f}")
+    return total, O.oracle_threads(), desc
+
+
+# ---------------------------------------------------------------- our arm
+
+
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    from paper_1510_07621_gb300 import P3M, build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOAD
+    n = w["n_p"] ** 3
+    seed = w["seed"] + rank
+    pos0, mom0 = S.zeldovich(w["n_p"], w["box"], w["a_begin"], seed)
+    sim = P3M(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"], softening=w["softening"],
+              precision=args.precision, stream=stream)
+    sim.set_particles(pos0, mom0, a=w["a_begin"])
+    a_s = S.log_spaced_steps(w["a_begin"], w["a_end"], w["setup_steps"])
+    t_setup = time.perf_counter()
+    for i in range(w["setup_steps"]):
+        sim.step(a_s[i], a_s[i + 1] - a_s[i])
+    torch.cuda.synchronize(dev)
+    t_setup = time.perf_counter() - t_setup
+    ratio = a_s[1] / a_s[0]
+    a = a_s[-1]
+    for _ in range(args.warmup):
+        sim.step(a, a * (ratio - 1.0))
+        a *= ratio
+    torch.cuda.synchronize(dev)
+
+    d0 = sim.diagnostics()
+    sim.set_timing(True)
+    sim.timings(reset=True)
+    phys = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    gpu_index = phys[local_rank] if len(phys) > local_rank and phys[local_rank] else local_rank
+    clocks = ClockSampler(gpu_index) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.step(a, a * (ratio - 1.0))
+        a *= ratio
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms_total = ev0.elapsed_time(ev1)
+    phases = sim.timings(reset=True)
+    sim.set_timing(False)
+    d1 = sim.diagnostics()
+
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n * world * args.steps / (ms_max / 1e3)
+
+    # ---- kernels and roofline (per launch = per step)
+    K = args.steps
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    alu_peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # FP32 TFLOP/s
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    pairs_per_step = (d1["pairs_total"] - d0["pairs_total"]) / K
+    M = w["mesh"]
+    nk = M * M * (M // 2 + 1)
+    passes = math.ceil(_key_bits(sim) / 8)
+    algo_bytes = {  # algorithmic bytes per launch of each HBM-bound phase
+        "kick_drift": 124 * n,
+        "sort": (16 + 20 * (passes - 1)) * n,
+        "permute": 128 * n,
+        "deposit": 32 * n,
+        "kspace": 32 * nk,
+        "gather": 60 * n,
+    }
+    kernels = {}
+    for name, ms in phases.items():
+        if ms <= 0:
+            continue
+        per = ms / K
+        entry = {"ms_per_launch": per, "share": ms / sum(phases.values())}
+        if name == "pairs":
+            entry.update(bound="alu", achieved=pairs_per_step * FLOPS_PER_PAIR / (per / 1e3) / 1e12,
+                         peak=alu_peak, unit="TFLOP/s", pairs_per_launch=pairs_per_step)
+        elif name in algo_bytes:
+            entry.update(bound="hbm", achieved=algo_bytes[name] / (per / 1e3) / 1e9,
+                         peak=hbm_peak, unit="GB/s")
+        if "achieved" in entry:
+            entry["frac"] = entry["achieved"] / entry["peak"]
+        kernels[name] = entry
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
+    tk = kernels[top]
+    roofline = None
+    if "achieved" in tk:
+        roofline = {"kernel": top, "bound": tk["bound"], "achieved": tk["achieved"],
+                    "peak": tk["peak"], "unit": tk["unit"], "frac": tk["frac"],
+                    "peak_source": f"{peak_kind}: " + ("SMs x 128 FP32 lanes x 2 x max SM clock"
+                                                        if tk["bound"] == "alu" else "hbm_gbs"),
+                    "traffic": _traffic(top)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 forces, f64 positions/momenta" if args.precision == "mixed" else "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "particles": n, "mesh": M,
+                      "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "per-step working set (~0.5 GB) larger than L2; no flush",
+                      "setup_s": t_setup},
+           "roofline": roofline, "kernels": kernels,
+           "gpu_launches": int(d1["launches"] - d0["launches"]),
+           "pairs_per_step": pairs_per_step, "max_cell_count": d1["max_cell_count"],
+           "clocks": clk}
+
+    # ---- e2e through the C ABI with pinned host buffers (rank 0 measures, others idle)
+    if rank == 0 and args.e2e_steps > 0:
+        hp = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+        hm = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+        ha = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+        sim.get_particles(hp, hm, ha)
+        a_e = a
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.set_particles(hp, hm, acc=ha, a=a_e)
+            sim.step(a_e, a_e * (ratio - 1.0))
+            a_e *= ratio
+            sim.get_particles(hp, hm, ha)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        out["e2e"] = {"value": n * args.e2e_steps / dt, "unit": UNIT, "steps": args.e2e_steps,
+                      "h2d_bytes_per_step": 72 * n, "d2h_bytes_per_step": 72 * n,
+                      "api": "p3m_set_particles(host pos, mom, acc) + p3m_step + "
+                             "p3m_get_particles(host pos, mom, acc)"}
+        snap_pos, snap_mom = hp.numpy().copy(), hm.numpy().copy()
+    else:
+        snap_pos = snap_mom = None
+
+    # ---- all-FP64 GPU mode on the same snapshot, and the force difference between the modes
+    if rank == 0 and args.fp64_steps > 0 and args.precision == "mixed":
+        hp = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+        hm = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+        sim.get_particles(hp, hm)
+        f32 = sim.forces(a)
+        with P3M(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"], softening=w["softening"],
+                 precision="fp64", stream=stream) as s64:
+            s64.set_particles(hp, hm, a=a)
+            f64 = s64.forces(a)
+            s64.step(a, a * (ratio - 1.0))
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            a64 = a * ratio
+            for _ in range(args.fp64_steps):
+                s64.step(a64, a64 * (ratio - 1.0))
+                a64 *= ratio
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        rms = math.sqrt(float(np.sum((f32 - f64) ** 2) / np.sum(f64 ** 2)))
+        out["fp64_gpu"] = {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                           "steps": args.fp64_steps,
+                           "mixed_vs_fp64_force_rel_rms": rms,
+                           "speedup_mixed_over_fp64": value / world / (n / (ms64 / 1e3))}
+        if snap_pos is None:
+            snap_pos, snap_mom = hp.numpy().copy(), hm.numpy().copy()
+
+    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        if snap_pos is None:
+            hp = np.empty((3, n))
+            hm = np.empty((3, n))
+            sim.get_particles(hp, hm)
+            snap_pos, snap_mom = hp, hm
+        sec, threads, desc = oracle_step_time(snap_pos, snap_mom, args.cpu_sample, 99)
+        out["cpu_baseline"] = {"value": n / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": desc + "; on the GPU run's a~1 snapshot",
+                               "seconds_per_step_estimate": sec}
+    sim.close()
+    return out
+
+
+def _key_bits(sim):
+    g = sim.geometry()
+    cells = g["n_c"] ** 3 << (3 * g["sub_bits"])
+    return max(1, int(cells - 1).bit_length())
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = {"pairs": "pair.cu", "deposit": "mesh.cu", "gather": "mesh.cu", "kspace": "mesh.cu",
+           "sort": "sort.cu", "permute": "sort.cu", "kick_drift": "sort.cu"}.get(kernel)
+    if not src or not os.path.exists(path):
+        return None
+    with open(os.path.join(ROOT, "paper_1510_07621_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(path) as f:
+        for line in f:
+            kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+            if kv.get("phase") == kernel and kv.get("source_sha") == sha:
+                return int(kv["bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------- reference arm (oracle)
+
+
+def run_reference(args):
+    from oracle import p3m_oracle as O
+    w = WORKLOAD
+    n = w["n_p"] ** 3
+    pos, mom = S.clustered(w["n_p"], w["box"], w["seed"])
+    for _ in range(args.warmup):
+        oracle_step_time(pos, mom, max(1000, args.cpu_sample // 4), 5)
+    total = 0.0
+    threads, desc = 1, ""
+    for k in range(args.steps):
+        sec, threads, desc = oracle_step_time(pos, mom, args.cpu_sample, 100 + k)
+        total += sec
+    value = n * args.steps / total
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME.split(";")[0] +
+                       "; synthetic clustered a=1 stand-in snapshot (no GPU evolution)",
+                       "particles": n, "mesh": w["mesh"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- main
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample", type=int, default=20000,
+                    help="particles whose pair sum the oracle times (0: skip the CPU baseline)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist = tdist
+    out = run_ours(args, rank, world, local_rank, dist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

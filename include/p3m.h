@@ -1,0 +1,209 @@
+/*
+ * p3m.h -- C ABI of the GB300 (sm_103a) P3M gravity step.
+ *
+ * The library evaluates the P3M force of the CONCEPT code (arXiv:1510.07621, the CONCEPT
+ * user's guide): particle-mesh long-range force plus a short-range particle-particle sum
+ * inside a cutoff, split at a Gaussian scale (Ch. Parameters, "Numerical parameters":
+ * PM_gridsize, PM_scale, P3M_cutoff, softeningfactors; "Simulation options": kick_algorithms
+ * 'PM' / 'P3M'), and advances comoving particles with a kick-drift-kick leapfrog over the
+ * scale factor (Ch. Parameters, "Cosmological parameters"; Ch. Snapshot Formats: comoving
+ * positions posx..posz and momenta momx..momz).  The guide prints no formulas; the
+ * arithmetic below is the textbook P3M method:
+ *
+ *   mesh:   CIC counts n(node), nodes at i*h, h = box/mesh
+ *           G(k) = -4 pi G m / h^3 * exp(-k^2 r_s^2) / k^2 / W(k)^2,  W = prod sinc^2(k_d h/2)
+ *           a_mesh,d = IFFT(-i k_d G(k) FFT(n - N/mesh^3)),  k_d = 0 on the Nyquist plane of d
+ *           a_LR(particle) = CIC interpolation of a_mesh
+ *   pairs:  a_SR,i = sum_{0 < |d_ij| < r_c} G m g(r/r_s) d_ij / (r^2 + eps^2)^(3/2),
+ *           g(x) = erfc(x/2) + x/sqrt(pi) exp(-x^2/4), d_ij the minimum-image separation
+ *   units:  time 1/H0 (H0 = 1), lengths as given (Mpc/h), G m = 3 Omega_m box^3 / (8 pi N)
+ *   motion: p = m a^2 dx/dt;  kick p += m a_grav int dt/a;  drift x += p/m int dt/a^2;
+ *           positions wrapped into [0, box)
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns P3M_OK (0) or a negative P3M_E* code; nothing throws across the
+ *     ABI.  After a failure p3m_last_error(ctx) holds a one-line message (for p3m_init, the
+ *     message is available through p3m_last_error(NULL)).
+ *   - Particle arrays are structure of arrays [3][n] of doubles: all x, then all y, then all
+ *     z.  Caller arrays are borrowed for the duration of the call only.
+ *   - on_device != 0: the pointers are CUDA device pointers on the current device; the call
+ *     returns with the work queued on the context's stream (host arrays: the call returns
+ *     after the copies completed).
+ *   - The context owns all device memory, cuFFT plans and events; p3m_free releases them.
+ *   - Particle order: the library keeps particles sorted by chaining cell internally; every
+ *     array a caller reads back is in the caller's original order (the order of
+ *     p3m_set_particles), except the sorted views of p3m_get_cells.
+ *   - Not thread-safe: one host thread at a time per context.
+ */
+#ifndef P3M_H
+#define P3M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define P3M_OK 0
+#define P3M_EINVAL (-1)     /* an argument is out of range; nothing was launched        */
+#define P3M_ENOMEM (-2)     /* a device allocation failed                               */
+#define P3M_ECUDA (-3)      /* a CUDA runtime call failed                               */
+#define P3M_ECUFFT (-4)     /* a cuFFT call failed                                      */
+#define P3M_ESTATE (-5)     /* call out of order (e.g. a step before any particles)     */
+#define P3M_ETIMEOUT (-6)   /* a bounded device-side wait gave up (error flag was set)  */
+#define P3M_ENONFINITE (-7) /* NaN or Inf in the particle input                         */
+
+/* precision modes */
+#define P3M_PREC_MIXED 0 /* FP32 mesh, FFTs and pair forces; FP64 positions, momenta and
+                            per-particle accumulators                                      */
+#define P3M_PREC_FP64 1  /* every step in FP64 (the all-FP64 comparison mode)              */
+
+typedef struct p3m_ctx p3m_ctx;
+
+/* Cosmological parameters (Ch. Parameters, "Cosmological parameters": H0, Omega_m,
+ * Omega_Lambda).  Curvature is 1 - omega_m - omega_lambda.  h0 only records the Hubble
+ * constant the caller's units refer to: internally time is measured in 1/H0. */
+typedef struct {
+    double omega_m;
+    double omega_lambda;
+    double h0;
+} p3m_cosmology;
+
+typedef struct {
+    int precision;      /* P3M_PREC_MIXED (default) or P3M_PREC_FP64                          */
+    double softening;   /* Plummer radius in units of the mean spacing box/N^(1/3)
+                           (Ch. Parameters, "softeningfactors"); default 0.02              */
+    int deconvolve_cic; /* 1 (default): divide G(k) by W(k)^2                              */
+    int short_range;    /* 1 (default): P3M; 0: pure PM ('PM' kick algorithm: no Gaussian
+                           filter, no pair sum)                                             */
+    int sub_bits;       /* b in 0..2: each chaining cell is split 2^b per side in the sort key
+                           (Morton order inside the cell); -1 = default (2)                */
+    void *stream;       /* cudaStream_t for all work of the context; NULL = legacy stream  */
+} p3m_options;
+
+/* Diagnostics of the current state (p3m_diagnostics). */
+typedef struct {
+    double momentum[3];   /* sum_i p_i (FP64, fixed reduction order)                       */
+    double kinetic;       /* sum_i |p_i|^2 / (2 m a^2)                                      */
+    double potential;     /* NaN: not computed by this version                              */
+    double layzer_irvine; /* NaN: not computed by this version                              */
+    double a;             /* scale factor of the state                                      */
+    uint64_t pairs;       /* ordered pairs inside r_c in the last force evaluation          */
+    uint64_t pairs_total; /* the same, summed over every force evaluation of the context   */
+    uint64_t launches;    /* kernels this library launched on the stream since p3m_init
+                             (cuFFT's own kernels not included)                             */
+    int64_t n;            /* number of particles                                            */
+    int32_t n_cells_side; /* chaining cells per side n_c                                    */
+    int32_t max_cell_count; /* most particles in one chaining cell (last sort)              */
+} p3m_diag;
+
+/* Fills *opt with the defaults listed above.  Returns P3M_EINVAL for NULL. */
+int p3m_default_options(p3m_options *opt);
+
+/*
+ * Creates a context for n particles in a periodic box.
+ *   box            side of the comoving box (Ch. Parameters, "boxsize"), > 0
+ *   n              number of particles, 1 <= n < 2^32
+ *   mesh           PM_gridsize M: even, 8 <= M <= 2048
+ *   r_s_cells      PM_scale: split scale r_s in mesh cells (> 0)
+ *   cutoff_in_rs   P3M_cutoff: r_c = cutoff_in_rs * r_s (> 0); with short_range the box must
+ *                  hold n_c = floor(box / r_c) >= 3 chaining cells per side
+ *   cosmo, opt     may be NULL (Einstein-de Sitter; p3m_default_options)
+ * Allocates every device buffer and plan up front (no allocation happens in later calls).
+ * Errors: P3M_EINVAL (arguments), P3M_ENOMEM, P3M_ECUFFT, P3M_ECUDA; *ctx is NULL then.
+ */
+int p3m_init(p3m_ctx **ctx, double box, int64_t n, int mesh, double r_s_cells,
+             double cutoff_in_rs, const p3m_cosmology *cosmo, const p3m_options *opt);
+
+/*
+ * Loads particles: pos3n and mom3n [3][n] (comoving positions; momenta m a^2 dx/dt), a
+ * common particle mass, and the scale factor a of the state.  Positions outside [0, box)
+ * are wrapped.  acc3n (nullable) supplies the accelerations at these positions (as returned
+ * by p3m_get_particles) so that the next p3m_step needs no extra force evaluation; without
+ * it the first p3m_step evaluates the forces at a first.
+ * Errors: P3M_EINVAL (NULL pointers, mass <= 0, a <= 0), P3M_ENONFINITE (NaN/Inf anywhere in
+ * the input; the state is then unusable until the next successful call), P3M_ECUDA.
+ * Synchronises the stream.
+ */
+int p3m_set_particles(p3m_ctx *ctx, const double *pos3n, const double *mom3n,
+                      const double *acc3n, double mass, double a, int on_device);
+
+/*
+ * Evaluates the accelerations (long + short range) at the current positions: sort, mesh
+ * force, pair force.  acc3n (nullable) receives them [3][n] in the caller's order.
+ * Errors: P3M_ESTATE (no particles), P3M_ECUDA, P3M_ECUFFT.
+ */
+int p3m_forces(p3m_ctx *ctx, double a, double *acc3n, int on_device);
+
+/*
+ * The same evaluation with the two parts returned separately (nullable each): acc_lr3n the
+ * mesh part, acc_sr3n the pair part.  Leaves the context's forces valid (their sum).
+ */
+int p3m_forces_split(p3m_ctx *ctx, double *acc_lr3n, double *acc_sr3n, int on_device);
+
+/*
+ * One kick-drift-kick step a -> a + da: half kick with the forces at a, drift, force
+ * evaluation at the new positions, half kick with them.  Queued on the stream without any
+ * host synchronisation (graph-capturable once forces are valid).
+ * Errors: P3M_EINVAL (a <= 0, da <= 0), P3M_ESTATE (no particles), P3M_ECUDA, P3M_ECUFFT.
+ */
+int p3m_step(p3m_ctx *ctx, double a, double da);
+
+/*
+ * Copies the state back in the caller's original particle order: pos3n, mom3n, acc3n
+ * (each nullable).  Host arrays: synchronises.  Returns P3M_ETIMEOUT if a device-side wait
+ * of an earlier call gave up.
+ */
+int p3m_get_particles(p3m_ctx *ctx, double *pos3n, double *mom3n, double *acc3n,
+                      int on_device);
+
+/* Momentum, kinetic energy, pair count and cell statistics of the current state.
+ * Synchronises the stream. */
+int p3m_diagnostics(p3m_ctx *ctx, p3m_diag *out);
+
+/*
+ * Sorted views of the last sort (after p3m_forces / p3m_step), for checking:
+ *   keys      [n]  sort keys in sorted order: (cell << 3b) | Morton(sub-cell), where
+ *                  cell = (c_z n_c + c_y) n_c + c_x
+ *   ids       [n]  original particle index of each sorted slot
+ *   cell_start[n_c^3 + 1] first sorted slot of each chaining cell; last entry n
+ * Each pointer nullable; all uint32.
+ */
+int p3m_get_cells(p3m_ctx *ctx, uint32_t *keys, uint32_t *ids, uint32_t *cell_start,
+                  int on_device);
+
+/*
+ * Copies a mesh of the last force evaluation: which = 0 the CIC count mesh minus its mean
+ * N/M^3, 1..3 the x/y/z mesh accelerations.  M^3 values, index (ix*M + iy)*M + iz, as float
+ * (P3M_PREC_MIXED) or double (P3M_PREC_FP64).
+ */
+int p3m_get_mesh(p3m_ctx *ctx, int which, void *out, int on_device);
+
+/* Number of chaining cells per side, mesh size and precision mode of the context. */
+int p3m_get_geometry(const p3m_ctx *ctx, int *n_c, int *mesh, int *precision, int *sub_bits);
+
+/*
+ * Per-phase device time.  p3m_set_timing(ctx, 1) records CUDA events on the context's stream
+ * around each phase of every later force evaluation and step; p3m_timings synchronises, adds
+ * the elapsed times per phase into ms[0..n-1] (milliseconds, summed since the last reset)
+ * and, with reset != 0, clears them.  Returns the number of phases (P3M_NPHASES).
+ */
+#define P3M_NPHASES 10
+int p3m_set_timing(p3m_ctx *ctx, int enable);
+int p3m_timings(p3m_ctx *ctx, double *ms, int n, int reset);
+/* Name of phase i ("kick_drift", "sort", "permute", "deposit", "fft_r2c", "kspace",
+ * "fft_c2r", "gather", "pairs", "other"), or NULL. */
+const char *p3m_phase_name(int i);
+
+/* Message of the last failure on ctx (ctx NULL: the last failed p3m_init).  Never NULL. */
+const char *p3m_last_error(const p3m_ctx *ctx);
+
+/* Releases everything the context owns.  NULL is ignored. */
+void p3m_free(p3m_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P3M_H */

@@ -1,0 +1,103 @@
+"""ctypes binding of ``libp3m.so``: the C ABI of ``include/p3m.h`` under the same names.
+
+Argument marshalling only; every step of the computation runs in the library's CUDA
+kernels.  There is no fallback: if the library cannot be loaded, ``load()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libp3m.so")
+
+P3M_OK = 0
+P3M_EINVAL = -1
+P3M_ENOMEM = -2
+P3M_ECUDA = -3
+P3M_ECUFFT = -4
+P3M_ESTATE = -5
+P3M_ETIMEOUT = -6
+P3M_ENONFINITE = -7
+P3M_PREC_MIXED = 0
+P3M_PREC_FP64 = 1
+P3M_NPHASES = 10
+
+# every symbol the header declares, with (restype, argtypes)
+_c = ctypes
+_vp = _c.c_void_p
+_dp = _c.c_void_p  # double*, passed as raw addresses (host or device)
+
+
+class Cosmology(_c.Structure):
+    _fields_ = [("omega_m", _c.c_double), ("omega_lambda", _c.c_double), ("h0", _c.c_double)]
+
+
+class Options(_c.Structure):
+    _fields_ = [("precision", _c.c_int), ("softening", _c.c_double),
+                ("deconvolve_cic", _c.c_int), ("short_range", _c.c_int),
+                ("sub_bits", _c.c_int), ("stream", _c.c_void_p)]
+
+
+class Diag(_c.Structure):
+    _fields_ = [("momentum", _c.c_double * 3), ("kinetic", _c.c_double),
+                ("potential", _c.c_double), ("layzer_irvine", _c.c_double), ("a", _c.c_double),
+                ("pairs", _c.c_uint64), ("pairs_total", _c.c_uint64), ("launches", _c.c_uint64),
+                ("n", _c.c_int64), ("n_cells_side", _c.c_int32),
+                ("max_cell_count", _c.c_int32)]
+
+
+SIGNATURES = {
+    "p3m_default_options": (_c.c_int, [_c.POINTER(Options)]),
+    "p3m_init": (_c.c_int, [_c.POINTER(_vp), _c.c_double, _c.c_int64, _c.c_int, _c.c_double,
+                            _c.c_double, _c.POINTER(Cosmology), _c.POINTER(Options)]),
+    "p3m_set_particles": (_c.c_int, [_vp, _dp, _dp, _dp, _c.c_double, _c.c_double, _c.c_int]),
+    "p3m_forces": (_c.c_int, [_vp, _c.c_double, _dp, _c.c_int]),
+    "p3m_forces_split": (_c.c_int, [_vp, _dp, _dp, _c.c_int]),
+    "p3m_step": (_c.c_int, [_vp, _c.c_double, _c.c_double]),
+    "p3m_get_particles": (_c.c_int, [_vp, _dp, _dp, _dp, _c.c_int]),
+    "p3m_diagnostics": (_c.c_int, [_vp, _c.POINTER(Diag)]),
+    "p3m_get_cells": (_c.c_int, [_vp, _vp, _vp, _vp, _c.c_int]),
+    "p3m_get_mesh": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int]),
+    "p3m_get_geometry": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
+                                    _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "p3m_set_timing": (_c.c_int, [_vp, _c.c_int]),
+    "p3m_timings": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.c_int, _c.c_int]),
+    "p3m_phase_name": (_c.c_char_p, [_c.c_int]),
+    "p3m_last_error": (_c.c_char_p, [_vp]),
+    "p3m_free": (None, [_vp]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libp3m.so (building it first is the caller's job: ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_1510_07621_gb300.build.build() "
+                           "(the P3M path has no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class P3MError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"P3M error {code}: {msg}")
+        self.code = code
+
+
+def check(code: int, ctx=None):
+    if code != P3M_OK:
+        msg = load().p3m_last_error(ctx).decode(errors="replace")
+        raise P3MError(code, msg)
+    return code

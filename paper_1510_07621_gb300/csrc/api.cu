@@ -1,0 +1,690 @@
+// C ABI of the P3M library: argument checks, the context (all device memory and cuFFT plans
+// allocated in p3m_init), and the order of the phases of a force evaluation and of a
+// kick-drift-kick step.  Every kernel launch goes to the context's stream.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "p3m_internal.cuh"
+
+namespace {
+
+char g_init_err[512] = "no error";
+
+int fail(p3m_ctx *c, int code, const char *fmt, ...)
+{
+    char *buf = c ? c->err : g_init_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(c, P3M_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+#define CKF(call)                                                                           \
+    do {                                                                                    \
+        cufftResult r_ = (call);                                                            \
+        if (r_ != CUFFT_SUCCESS) return fail(c, P3M_ECUFFT, "%s failed: cufft code %d", #call, (int)r_); \
+    } while (0)
+
+// ---------------------------------------------------------------- cosmology (host, FP64)
+
+bool is_eds(const p3m_cosmology &cs) { return cs.omega_m == 1.0 && cs.omega_lambda == 0.0; }
+
+double hubble(const p3m_cosmology &cs, double a)
+{
+    const double ok = 1.0 - cs.omega_m - cs.omega_lambda;
+    return sqrt(cs.omega_m / (a * a * a) + ok / (a * a) + cs.omega_lambda);
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n from the
+// Chebyshev-point initial guesses).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+double quad(const p3m_cosmology &cs, double a1, double a2, int power)
+{
+    static std::vector<double> xg, wg;
+    if (xg.empty()) gauss_legendre(48, xg, wg);
+    double s = 0.0;
+    for (size_t i = 0; i < xg.size(); ++i) {
+        const double a = 0.5 * (a2 - a1) * xg[i] + 0.5 * (a2 + a1);
+        s += wg[i] / (pow(a, power) * hubble(cs, a));
+    }
+    return 0.5 * (a2 - a1) * s;
+}
+
+// ---------------------------------------------------------------- phase timing
+
+struct Phase {
+    p3m_ctx *c;
+    int id;
+    Phase(p3m_ctx *c_, int id_) : c(c_), id(id_)
+    {
+        if (c->timing && c->ev_used + 2 <= c->ev_cap) {
+            cudaEventRecord(c->ev[c->ev_used], c->stream);
+            c->ev_phase[c->ev_used] = id;
+        } else {
+            id = -1;
+        }
+    }
+    ~Phase()
+    {
+        if (id >= 0) {
+            cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+            c->ev_phase[c->ev_used + 1] = id;
+            c->ev_used += 2;
+        }
+    }
+};
+
+void harvest(p3m_ctx *c)
+{
+    if (c->ev_used == 0) return;
+    cudaEventSynchronize(c->ev[c->ev_used - 1]);
+    for (int i = 0; i + 1 < c->ev_used; i += 2) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess)
+            c->phase_ms[c->ev_phase[i]] += ms;
+    }
+    c->ev_used = 0;
+}
+
+const char *kPhaseNames[P3M_NPHASES] = {"kick_drift", "sort",   "permute", "deposit", "fft_r2c",
+                                        "kspace",     "fft_c2r", "gather", "pairs",   "other"};
+
+// ---------------------------------------------------------------- context lifetime
+
+void release(p3m_ctx *c)
+{
+    void *bufs[] = {c->pos,       c->mom,      c->acc,          c->acc_lr,   c->pid,
+                    c->pos_alt,   c->mom_alt,  c->pid_alt,      c->rel,      c->keys,
+                    c->keys_alt,  c->vals,     c->vals_alt,     c->digit_counts, c->scan_aux,
+                    c->cell_start, c->work,    c->work_off,     c->counters, c->pair_count,
+                    c->red,       c->rho,      c->rho_k,        c->frc_k,    c->frc,
+                    c->tab_k,     c->tab_kg,   c->tab_g};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (c->plans_made) {
+        cufftDestroy(c->plan_r2c);
+        cufftDestroy(c->plan_c2r);
+    }
+    if (c->ev) {
+        for (int i = 0; i < c->ev_cap; ++i) cudaEventDestroy(c->ev[i]);
+        free(c->ev);
+        free(c->ev_phase);
+    }
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t bytes)
+{
+    *p = nullptr;
+    return cudaMalloc((void **)p, bytes < 16 ? 16 : bytes);
+}
+
+int check_flags(p3m_ctx *c)
+{
+    uint32_t flags = 0;
+    CK(cudaMemcpyAsync(&flags, c->counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (flags & P3M_FLAG_TIMEOUT) return fail(c, P3M_ETIMEOUT, "a bounded device-side wait gave up");
+    return P3M_OK;
+}
+
+// ---------------------------------------------------------------- force evaluation
+// Sort by cell, mesh force, pair force.  Positions must already be wrapped and keyed
+// (c->keys).  Result: c->acc (total), c->acc_lr (mesh part).  kfac != 0: the final half kick
+// mom += kfac * acc is fused into the last kernel.
+int evaluate(p3m_ctx *c, double kfac, double *sr_only_out)
+{
+    {
+        Phase ph(c, PH_SORT);
+        CK(launch_radix_sort(c));
+    }
+    {
+        Phase ph(c, PH_PERMUTE);
+        CK(launch_permute_and_cells(c));
+    }
+    c->sorted_valid = true;
+    {
+        Phase ph(c, PH_DEPOSIT);
+        CK(launch_deposit(c));
+    }
+    {
+        Phase ph(c, PH_FFT_R2C);
+        CKF(c->precision == P3M_PREC_MIXED
+                ? cufftExecR2C(c->plan_r2c, (cufftReal *)c->rho, (cufftComplex *)c->rho_k)
+                : cufftExecD2Z(c->plan_r2c, (cufftDoubleReal *)c->rho, (cufftDoubleComplex *)c->rho_k));
+    }
+    {
+        Phase ph(c, PH_KSPACE);
+        CK(launch_kspace(c));
+    }
+    {
+        Phase ph(c, PH_FFT_C2R);
+        CKF(c->precision == P3M_PREC_MIXED
+                ? cufftExecC2R(c->plan_c2r, (cufftComplex *)c->frc_k, (cufftReal *)c->frc)
+                : cufftExecZ2D(c->plan_c2r, (cufftDoubleComplex *)c->frc_k, (cufftDoubleReal *)c->frc));
+    }
+    if (c->short_range) {
+        {
+            Phase ph(c, PH_GATHER);
+            CK(launch_gather(c, c->acc_lr));
+        }
+        Phase ph(c, PH_PAIRS);
+        if (sr_only_out) {
+            CK(launch_pairs(c, nullptr, sr_only_out, 0.0));
+        } else {
+            CK(launch_pairs(c, c->acc_lr, c->acc, kfac));
+        }
+    } else {
+        // pure PM: the mesh part is the whole force
+        {
+            Phase ph(c, PH_GATHER);
+            CK(launch_gather(c, sr_only_out ? c->acc_lr : c->acc));
+        }
+        if (sr_only_out) CK(cudaMemsetAsync(sr_only_out, 0, 3 * sizeof(double) * c->g.n, c->stream));
+        if (kfac != 0.0) {
+            Phase ph(c, PH_OTHER);
+            CK(launch_kick(c, kfac));
+        }
+    }
+    return P3M_OK;
+}
+
+int key_current(p3m_ctx *c)
+{
+    Phase ph(c, PH_KICK_DRIFT);
+    CK(launch_kick_drift_keys(c, false, 0.0, 0.0));
+    return P3M_OK;
+}
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host cosmology helpers
+
+double p3m_kick_factor(const p3m_cosmology &cs, double a1, double a2)
+{
+    if (is_eds(cs)) return 2.0 * (sqrt(a2) - sqrt(a1));
+    return quad(cs, a1, a2, 2);
+}
+
+double p3m_drift_factor(const p3m_cosmology &cs, double a1, double a2)
+{
+    if (is_eds(cs)) return 2.0 * (1.0 / sqrt(a1) - 1.0 / sqrt(a2));
+    return quad(cs, a1, a2, 3);
+}
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" int p3m_default_options(p3m_options *opt)
+{
+    if (!opt) return P3M_EINVAL;
+    opt->precision = P3M_PREC_MIXED;
+    opt->softening = 0.02;
+    opt->deconvolve_cic = 1;
+    opt->short_range = 1;
+    opt->sub_bits = 2;
+    opt->stream = nullptr;
+    return P3M_OK;
+}
+
+extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r_s_cells,
+                        double cutoff_in_rs, const p3m_cosmology *cosmo, const p3m_options *opt_in)
+{
+    p3m_ctx *c = nullptr;
+    if (!out) return fail(c, P3M_EINVAL, "p3m_init: ctx pointer is NULL");
+    *out = nullptr;
+    p3m_options opt;
+    p3m_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.sub_bits < 0) opt.sub_bits = 2;
+    p3m_cosmology cs = {1.0, 0.0, 100.0};
+    if (cosmo) cs = *cosmo;
+
+    if (!finite_pos(box)) return fail(c, P3M_EINVAL, "p3m_init: box must be finite and > 0");
+    if (n < 1 || n >= (int64_t)1 << 32) return fail(c, P3M_EINVAL, "p3m_init: n must be in [1, 2^32)");
+    if (mesh < 8 || mesh > 2048 || (mesh & 1))
+        return fail(c, P3M_EINVAL, "p3m_init: mesh must be even and in [8, 2048]");
+    if (!finite_pos(r_s_cells)) return fail(c, P3M_EINVAL, "p3m_init: r_s_cells must be > 0");
+    if (!finite_pos(cutoff_in_rs)) return fail(c, P3M_EINVAL, "p3m_init: cutoff_in_rs must be > 0");
+    if (opt.precision != P3M_PREC_MIXED && opt.precision != P3M_PREC_FP64)
+        return fail(c, P3M_EINVAL, "p3m_init: unknown precision mode");
+    if (!(opt.softening >= 0.0) || !isfinite(opt.softening))
+        return fail(c, P3M_EINVAL, "p3m_init: softening must be >= 0");
+    if (opt.sub_bits > 2) return fail(c, P3M_EINVAL, "p3m_init: sub_bits must be in 0..2");
+    if (!finite_pos(cs.omega_m) || !(cs.omega_lambda >= 0.0) || !isfinite(cs.omega_lambda))
+        return fail(c, P3M_EINVAL, "p3m_init: need omega_m > 0 and omega_lambda >= 0");
+
+    P3MGeom g;
+    memset(&g, 0, sizeof(g));
+    g.box = box;
+    g.n = n;
+    g.mesh = mesh;
+    g.inv_h = (double)mesh / box;
+    g.r_s = r_s_cells * (box / mesh);
+    g.r_c = cutoff_in_rs * (r_s_cells * (box / mesh));
+    g.eps = opt.softening * (box / cbrt((double)n));
+    g.gm = 3.0 * cs.omega_m * pow(box, 3.0) / (8.0 * M_PI * (double)n);
+    if (opt.short_range) {
+        const double ncd = floor(box / g.r_c);
+        if (ncd < 3.0)
+            return fail(c, P3M_EINVAL,
+                        "p3m_init: box/r_c = %.4g: need at least 3 chaining cells per side", box / g.r_c);
+        if (ncd > 1024.0) return fail(c, P3M_EINVAL, "p3m_init: more than 1024 chaining cells per side");
+        g.n_c = (int)ncd;
+    } else {
+        g.n_c = mesh / 6 < 3 ? 3 : (mesh / 6 > 1024 ? 1024 : mesh / 6);
+    }
+    g.sub_bits = opt.sub_bits;
+    g.n_fine = g.n_c << g.sub_bits;
+    g.inv_fine = (double)g.n_fine / box;
+    g.cs = box / g.n_c;
+    g.n_cells = g.n_c * g.n_c * g.n_c;
+    g.mean_count = (double)n / ((double)mesh * mesh * mesh);
+    int key_bits = 0;
+    {
+        const uint64_t max_key = ((uint64_t)g.n_cells << (3 * g.sub_bits)) - 1;
+        if (max_key >= (1ull << 32)) return fail(c, P3M_EINVAL, "p3m_init: sort key exceeds 32 bits");
+        while (key_bits < 32 && (max_key >> key_bits)) ++key_bits;
+        if (key_bits == 0) key_bits = 1;
+    }
+
+    c = (p3m_ctx *)calloc(1, sizeof(p3m_ctx));
+    if (!c) return fail(nullptr, P3M_ENOMEM, "p3m_init: host allocation failed");
+    c->g = g;
+    c->precision = opt.precision;
+    c->deconvolve = opt.deconvolve_cic ? 1 : 0;
+    c->short_range = opt.short_range ? 1 : 0;
+    c->cosmo = cs;
+    c->mass = 1.0;
+    c->a = 1.0;
+    c->stream = (cudaStream_t)opt.stream;
+    c->key_bits = key_bits;
+    strcpy(c->err, "no error");
+
+    int rc = P3M_OK;
+    do {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) {
+            rc = fail(nullptr, P3M_ECUDA, "p3m_init: no CUDA device: %s", cudaGetErrorString(e));
+            break;
+        }
+        const size_t N = (size_t)n, M = (size_t)mesh, nk = M * M * (M / 2 + 1), M3 = M * M * M;
+        const size_t real = c->precision == P3M_PREC_MIXED ? 4 : 8;
+        c->n_tiles = (int)((N + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
+        c->max_work = N / P3M_PAIR_TI + (size_t)g.n_cells + 1;
+        const size_t scan_n = (size_t)256 * c->n_tiles > (size_t)g.n_cells + 1 ? (size_t)256 * c->n_tiles
+                                                                               : (size_t)g.n_cells + 1;
+        struct {
+            void **p;
+            size_t bytes;
+        } allocs[] = {
+            {(void **)&c->pos, 24 * N},       {(void **)&c->mom, 24 * N},
+            {(void **)&c->acc, 24 * N},       {(void **)&c->acc_lr, 24 * N},
+            {(void **)&c->pos_alt, 24 * N},   {(void **)&c->mom_alt, 24 * N},
+            {(void **)&c->pid, 4 * N},        {(void **)&c->pid_alt, 4 * N},
+            {(void **)&c->rel, 4 * real * N}, {(void **)&c->keys, 4 * N},
+            {(void **)&c->keys_alt, 4 * N},   {(void **)&c->vals, 4 * N},
+            {(void **)&c->vals_alt, 4 * N},   {(void **)&c->digit_counts, 4 * 256 * (size_t)c->n_tiles},
+            {(void **)&c->scan_aux, 4 * (scan_n / P3M_SORT_TILE + 4)},
+            {(void **)&c->cell_start, 4 * ((size_t)g.n_cells + 1)},
+            {(void **)&c->work, 8 * c->max_work}, {(void **)&c->work_off, 4 * ((size_t)g.n_cells + 1)},
+            {(void **)&c->counters, 16},      {(void **)&c->pair_count, 16},
+            {(void **)&c->red, 8 * (1024 * 4 + 8)},
+            {(void **)&c->rho, real * M3},    {(void **)&c->rho_k, 2 * real * nk},
+            {(void **)&c->frc_k, 6 * real * nk}, {(void **)&c->frc, 3 * real * M3},
+            {(void **)&c->tab_k, real * M},   {(void **)&c->tab_kg, real * M},
+            {(void **)&c->tab_g, real * M},
+        };
+        for (auto &a : allocs) {
+            e = dalloc(a.p, a.bytes);
+            if (e != cudaSuccess) {
+                rc = fail(nullptr, P3M_ENOMEM, "p3m_init: cudaMalloc of %zu bytes failed: %s", a.bytes,
+                          cudaGetErrorString(e));
+                break;
+            }
+        }
+        if (rc != P3M_OK) break;
+        cudaMemsetAsync(c->counters, 0, 16, c->stream);
+        cudaMemsetAsync(c->pair_count, 0, 16, c->stream);
+
+        // per-axis tables (FP64 on the host, stored in the mesh precision)
+        const double h = box / mesh, rs2 = c->short_range ? g.r_s * g.r_s : 0.0;
+        std::vector<double> tk(M), tkg(M), tg(M);
+        for (int i = 0; i < mesh; ++i) {
+            const int m = i <= mesh / 2 ? i : i - mesh;
+            const double k = 2.0 * M_PI / box * m;
+            tk[i] = k;
+            tkg[i] = (i == mesh / 2) ? 0.0 : k;
+            double t = exp(-k * k * rs2);
+            if (c->deconvolve) {
+                const double x = 0.5 * k * h;
+                const double s = x == 0.0 ? 1.0 : sin(x) / x;
+                t /= (s * s) * (s * s);
+            }
+            tg[i] = t;
+        }
+        c->green_const = -4.0 * M_PI * (g.gm / (h * h * h)) / ((double)M3);
+        if (c->precision == P3M_PREC_MIXED) {
+            std::vector<float> f(M);
+            const std::vector<double> *src[3] = {&tk, &tkg, &tg};
+            void *dst[3] = {c->tab_k, c->tab_kg, c->tab_g};
+            for (int t = 0; t < 3; ++t) {
+                for (size_t i = 0; i < M; ++i) f[i] = (float)(*src[t])[i];
+                e = cudaMemcpy(dst[t], f.data(), 4 * M, cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) break;
+            }
+        } else {
+            e = cudaMemcpy(c->tab_k, tk.data(), 8 * M, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->tab_kg, tkg.data(), 8 * M, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->tab_g, tg.data(), 8 * M, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            rc = fail(nullptr, P3M_ECUDA, "p3m_init: table upload failed: %s", cudaGetErrorString(e));
+            break;
+        }
+
+        // cuFFT: one R2C, and the three C2R as one batch of 3 (default layouts)
+        int dims[3] = {mesh, mesh, mesh};
+        cufftResult r = cufftPlan3d(&c->plan_r2c, mesh, mesh, mesh,
+                                    c->precision == P3M_PREC_MIXED ? CUFFT_R2C : CUFFT_D2Z);
+        if (r == CUFFT_SUCCESS) {
+            r = cufftPlanMany(&c->plan_c2r, 3, dims, nullptr, 1, (int)nk, nullptr, 1, (int)M3,
+                              c->precision == P3M_PREC_MIXED ? CUFFT_C2R : CUFFT_Z2D, 3);
+            if (r != CUFFT_SUCCESS) cufftDestroy(c->plan_r2c);
+        }
+        if (r != CUFFT_SUCCESS) {
+            rc = fail(nullptr, P3M_ECUFFT, "p3m_init: cuFFT plan creation failed (code %d)", (int)r);
+            break;
+        }
+        c->plans_made = true;
+        cufftSetStream(c->plan_r2c, c->stream);
+        cufftSetStream(c->plan_c2r, c->stream);
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            rc = fail(nullptr, P3M_ECUDA, "p3m_init: %s", cudaGetErrorString(e));
+            break;
+        }
+    } while (0);
+    if (rc != P3M_OK) {
+        release(c);
+        free(c);
+        return rc;
+    }
+    *out = c;
+    return P3M_OK;
+}
+
+extern "C" int p3m_set_particles(p3m_ctx *c, const double *pos, const double *mom,
+                                 const double *acc, double mass, double a, int on_device)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!pos || !mom) return fail(c, P3M_EINVAL, "p3m_set_particles: pos and mom are required");
+    if (!finite_pos(mass)) return fail(c, P3M_EINVAL, "p3m_set_particles: mass must be > 0");
+    if (!finite_pos(a)) return fail(c, P3M_EINVAL, "p3m_set_particles: a must be > 0");
+    const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
+    CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(uint32_t), c->stream));
+    const double *sp = pos, *sm = mom, *sa = acc;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->pos_alt, pos, bytes, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->mom_alt, mom, bytes, cudaMemcpyHostToDevice, c->stream));
+        sp = c->pos_alt;
+        sm = c->mom_alt;
+        if (acc) {
+            CK(cudaMemcpyAsync(c->acc_lr, acc, bytes, cudaMemcpyHostToDevice, c->stream));
+            sa = c->acc_lr;
+        }
+    }
+    CK(launch_load_particles(c, sp, sm, sa));
+    uint32_t flags = 0;
+    CK(cudaMemcpyAsync(&flags, c->counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_particles = false;
+    c->forces_valid = false;
+    c->sorted_valid = false;
+    if (flags & P3M_FLAG_NONFINITE) {
+        cudaMemsetAsync(c->counters + 1, 0, sizeof(uint32_t), c->stream);
+        return fail(c, P3M_ENONFINITE, "p3m_set_particles: NaN or Inf in the input");
+    }
+    c->mass = mass;
+    c->a = a;
+    c->have_particles = true;
+    c->forces_valid = acc != nullptr;
+    return P3M_OK;
+}
+
+extern "C" int p3m_forces(p3m_ctx *c, double a, double *acc3n, int on_device)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_forces: no particles loaded");
+    if (!finite_pos(a)) return fail(c, P3M_EINVAL, "p3m_forces: a must be > 0");
+    int rc = key_current(c);
+    if (rc) return rc;
+    rc = evaluate(c, 0.0, nullptr);
+    if (rc) return rc;
+    c->forces_valid = true;
+    c->a = a;
+    if (acc3n) return p3m_get_particles(c, nullptr, nullptr, acc3n, on_device);
+    return P3M_OK;
+}
+
+extern "C" int p3m_forces_split(p3m_ctx *c, double *acc_lr, double *acc_sr, int on_device)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_forces_split: no particles loaded");
+    int rc = key_current(c);
+    if (rc) return rc;
+    rc = evaluate(c, 0.0, c->acc);  // c->acc = short-range part only
+    if (rc) return rc;
+    const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
+    double *outs[2] = {acc_lr, acc_sr};
+    const double *srcs[2] = {c->acc_lr, c->acc};
+    for (int t = 0; t < 2; ++t) {
+        if (!outs[t]) continue;
+        if (on_device) {
+            CK(launch_scatter_out(c, srcs[t], outs[t]));
+        } else {
+            CK(launch_scatter_out(c, srcs[t], c->pos_alt));
+            CK(cudaMemcpyAsync(outs[t], c->pos_alt, bytes, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    }
+    CK(launch_axpy(c, c->acc, c->acc_lr, 1.0));  // total
+    c->forces_valid = true;
+    return check_flags(c);
+}
+
+extern "C" int p3m_step(p3m_ctx *c, double a, double da)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_step: no particles loaded");
+    if (!finite_pos(a) || !finite_pos(da)) return fail(c, P3M_EINVAL, "p3m_step: need a > 0, da > 0");
+    int rc;
+    if (!c->forces_valid) {
+        rc = key_current(c);
+        if (rc) return rc;
+        rc = evaluate(c, 0.0, nullptr);
+        if (rc) return rc;
+        c->forces_valid = true;
+    }
+    const double am = a + 0.5 * da, a2 = a + da;
+    const double k1 = c->mass * p3m_kick_factor(c->cosmo, a, am);
+    const double dfac = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
+    const double k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+    {
+        Phase ph(c, PH_KICK_DRIFT);
+        CK(launch_kick_drift_keys(c, true, k1, dfac));
+    }
+    rc = evaluate(c, k2, nullptr);
+    if (rc) return rc;
+    c->a = a2;
+    return P3M_OK;
+}
+
+extern "C" int p3m_get_particles(p3m_ctx *c, double *pos, double *mom, double *acc, int on_device)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_get_particles: no particles loaded");
+    if (acc && !c->forces_valid) return fail(c, P3M_ESTATE, "p3m_get_particles: forces not evaluated");
+    const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
+    double *outs[3] = {pos, mom, acc};
+    const double *srcs[3] = {c->pos, c->mom, c->acc};
+    for (int t = 0; t < 3; ++t) {
+        if (!outs[t]) continue;
+        if (on_device) {
+            CK(launch_scatter_out(c, srcs[t], outs[t]));
+        } else {
+            double *stage = t == 0 ? c->pos_alt : (t == 1 ? c->mom_alt : c->acc_lr);
+            CK(launch_scatter_out(c, srcs[t], stage));
+            CK(cudaMemcpyAsync(outs[t], stage, bytes, cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    if (!on_device) return check_flags(c);
+    return P3M_OK;
+}
+
+extern "C" int p3m_diagnostics(p3m_ctx *c, p3m_diag *out)
+{
+    if (!c || !out) return fail(c, P3M_EINVAL, "p3m_diagnostics: NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->potential = NAN;
+    out->layzer_irvine = NAN;
+    out->a = c->a;
+    out->n = c->g.n;
+    out->n_cells_side = c->g.n_c;
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_diagnostics: no particles loaded");
+    double r[4];
+    CK(launch_diag(c, r));
+    out->momentum[0] = r[0];
+    out->momentum[1] = r[1];
+    out->momentum[2] = r[2];
+    out->kinetic = r[3] / (2.0 * c->mass * c->a * c->a);
+    unsigned long long pc[2] = {0, 0};
+    uint32_t mc = 0;
+    CK(cudaMemcpy(pc, c->pair_count, sizeof(pc), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&mc, c->counters + 2, sizeof(mc), cudaMemcpyDeviceToHost));
+    out->pairs = pc[0];
+    out->pairs_total = pc[1];
+    out->launches = c->launches;
+    out->max_cell_count = (int32_t)mc;
+    return check_flags(c);
+}
+
+extern "C" int p3m_get_cells(p3m_ctx *c, uint32_t *keys, uint32_t *ids, uint32_t *cell_start,
+                             int on_device)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!c->sorted_valid) return fail(c, P3M_ESTATE, "p3m_get_cells: nothing sorted yet");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t n = (size_t)c->g.n;
+    if (keys) CK(cudaMemcpyAsync(keys, c->keys, 4 * n, kind, c->stream));
+    if (ids) CK(cudaMemcpyAsync(ids, c->pid, 4 * n, kind, c->stream));
+    if (cell_start)
+        CK(cudaMemcpyAsync(cell_start, c->cell_start, 4 * ((size_t)c->g.n_cells + 1), kind, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return P3M_OK;
+}
+
+extern "C" int p3m_get_mesh(p3m_ctx *c, int which, void *out, int on_device)
+{
+    if (!c || !out) return fail(c, P3M_EINVAL, "p3m_get_mesh: NULL argument");
+    if (which < 0 || which > 3) return fail(c, P3M_EINVAL, "p3m_get_mesh: which must be 0..3");
+    if (!c->sorted_valid) return fail(c, P3M_ESTATE, "p3m_get_mesh: no force evaluation yet");
+    const size_t M3 = (size_t)c->g.mesh * c->g.mesh * c->g.mesh;
+    const size_t real = c->precision == P3M_PREC_MIXED ? 4 : 8;
+    const char *src = which == 0 ? (const char *)c->rho : (const char *)c->frc + (which - 1) * M3 * real;
+    CK(cudaMemcpyAsync(out, src, M3 * real, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return P3M_OK;
+}
+
+extern "C" int p3m_get_geometry(const p3m_ctx *c, int *n_c, int *mesh, int *precision, int *sub_bits)
+{
+    if (!c) return P3M_EINVAL;
+    if (n_c) *n_c = c->g.n_c;
+    if (mesh) *mesh = c->g.mesh;
+    if (precision) *precision = c->precision;
+    if (sub_bits) *sub_bits = c->g.sub_bits;
+    return P3M_OK;
+}
+
+extern "C" int p3m_set_timing(p3m_ctx *c, int enable)
+{
+    if (!c) return P3M_EINVAL;
+    if (enable && !c->ev) {
+        c->ev_cap = 8192;
+        c->ev = (cudaEvent_t *)calloc(c->ev_cap, sizeof(cudaEvent_t));
+        c->ev_phase = (int *)calloc(c->ev_cap, sizeof(int));
+        if (!c->ev || !c->ev_phase) return fail(c, P3M_ENOMEM, "p3m_set_timing: host allocation failed");
+        for (int i = 0; i < c->ev_cap; ++i) CK(cudaEventCreate(&c->ev[i]));
+    }
+    if (!enable && c->ev) harvest(c);
+    c->timing = enable != 0;
+    return P3M_OK;
+}
+
+extern "C" int p3m_timings(p3m_ctx *c, double *ms, int n, int reset)
+{
+    if (!c) return P3M_EINVAL;
+    harvest(c);
+    for (int i = 0; i < n && i < P3M_NPHASES; ++i) ms[i] = c->phase_ms[i];
+    if (reset)
+        for (int i = 0; i < P3M_NPHASES; ++i) c->phase_ms[i] = 0.0;
+    return P3M_NPHASES;
+}
+
+extern "C" const char *p3m_phase_name(int i)
+{
+    return (i >= 0 && i < P3M_NPHASES) ? kPhaseNames[i] : nullptr;
+}
+
+extern "C" const char *p3m_last_error(const p3m_ctx *c) { return c ? c->err : g_init_err; }
+
+extern "C" void p3m_free(p3m_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+    free(c);
+}

@@ -1,0 +1,165 @@
+// Kick, particle load/unload in the caller's order, and FP64 diagnostics reductions.
+#include <cuda_runtime.h>
+
+#include "p3m_internal.cuh"
+
+namespace {
+
+inline int grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+__global__ void k_kick(double *__restrict__ mom, const double *__restrict__ acc, int64_t n3,
+                       double kfac)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x)
+        mom[i] = __dadd_rn(mom[i], __dmul_rn(kfac, acc[i]));
+}
+
+__device__ __forceinline__ double wrap_box(double x, double L)
+{
+    x = fmod(x, L);
+    if (x < 0.0) x = __dadd_rn(x, L);
+    if (x >= L) x = __dadd_rn(x, -L);
+    return x;
+}
+
+// Copies caller arrays into slot order = caller order, wraps positions, identity ids,
+// and flags any NaN/Inf.
+__global__ void k_load(const double *__restrict__ pos, const double *__restrict__ mom,
+                       const double *__restrict__ acc, int64_t n, double L,
+                       double *__restrict__ pos_out, double *__restrict__ mom_out,
+                       double *__restrict__ acc_out, uint32_t *__restrict__ pid,
+                       uint32_t *__restrict__ flags)
+{
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double x = pos[d * n + i], p = mom[d * n + i];
+            bad |= !isfinite(x) || !isfinite(p);
+            pos_out[d * n + i] = isfinite(x) ? wrap_box(x, L) : 0.0;
+            mom_out[d * n + i] = p;
+            if (acc) {
+                const double a = acc[d * n + i];
+                bad |= !isfinite(a);
+                acc_out[d * n + i] = a;
+            }
+        }
+        pid[i] = (uint32_t)i;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, P3M_FLAG_NONFINITE);
+}
+
+// dst[d][pid[k]] = src[d][k]
+__global__ void k_scatter(const double *__restrict__ src, const uint32_t *__restrict__ pid,
+                          int64_t n, double *__restrict__ dst)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = pid[k];
+        dst[j] = src[k];
+        dst[n + j] = src[n + k];
+        dst[2 * n + j] = src[2 * n + k];
+    }
+}
+
+// Per-block partial sums of (px, py, pz, |p|^2) in a fixed order; then one block adds the
+// partials in block order.  Same result on every run.
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 1024;
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_diag_partial(const double *__restrict__ mom, int64_t n, double *__restrict__ part)
+{
+    __shared__ double s[4][kRedThreads];
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double px = mom[i], py = mom[n + i], pz = mom[2 * n + i];
+        acc[0] += px;
+        acc[1] += py;
+        acc[2] += pz;
+        acc[3] += px * px + py * py + pz * pz;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_diag_final(double *part, int nb)
+{
+    __shared__ double s[4][kRedThreads];
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += part[b * 4 + q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[kRedBlocks * 4 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+}  // namespace
+
+cudaError_t launch_axpy(p3m_ctx *c, double *y, const double *x, double alpha)
+{
+    c->launches += 1;
+    const int64_t n3 = 3 * c->g.n;
+    k_kick<<<grid_for(n3, 256, c->num_sms), 256, 0, c->stream>>>(y, x, n3, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick(p3m_ctx *c, double kfac)
+{
+    c->launches += 1;
+    const int64_t n3 = 3 * c->g.n;
+    k_kick<<<grid_for(n3, 256, c->num_sms), 256, 0, c->stream>>>(c->mom, c->acc, n3, kfac);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_particles(p3m_ctx *c, const double *pos, const double *mom,
+                                  const double *acc)
+{
+    c->launches += 1;
+    k_load<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+        pos, mom, acc, c->g.n, c->g.box, c->pos, c->mom, c->acc, c->pid, c->counters + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst)
+{
+    c->launches += 1;
+    k_scatter<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(src, c->pid, c->g.n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(p3m_ctx *c, double *host_out)
+{
+    c->launches += 2;
+    k_diag_partial<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->mom, c->g.n, c->red);
+    k_diag_final<<<1, kRedThreads, 0, c->stream>>>(c->red, kRedBlocks);
+    cudaError_t e = cudaMemcpyAsync(host_out, c->red + kRedBlocks * 4, 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}

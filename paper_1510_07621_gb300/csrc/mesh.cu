@@ -1,0 +1,272 @@
+// Particle-mesh part of the P3M force (the guide's PM_gridsize mesh, Ch. Parameters):
+// CIC mass assignment, the fused k-space pass (Green's function with the Gaussian long-range
+// filter of scale PM_scale, CIC deconvolution, spectral gradient) and the CIC interpolation
+// of the three mesh accelerations back to the particles.  cuFFT does the transforms.
+//
+// Mesh layout: M^3 values, node (ix, iy, iz) at ((ix*M + iy)*M + iz), node positions i*h.
+// Spectrum layout (cuFFT R2C): M * M * (M/2+1) complex values, z fastest.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include "p3m_internal.cuh"
+
+namespace {
+
+template <typename T>
+__global__ void k_fill(T *__restrict__ a, size_t n, T v)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+__device__ __forceinline__ int wrap_index(int i, int M)
+{
+    i %= M;
+    return i < 0 ? i + M : i;
+}
+
+// CIC stencil of a wrapped position: base node i0 = floor(x M/L) and fraction f.
+template <typename T>
+__device__ __forceinline__ void cic_stencil(double x, double inv_h, int &i0, T &f)
+{
+    const double u = __dmul_rn(x, inv_h);
+    const double fl = floor(u);
+    i0 = (int)fl;
+    f = (T)(u - fl);
+}
+
+// One CTA per chaining cell: the cell's particles accumulate into a W^3 node tile in shared
+// memory (tile origin one node below the cell's first node), which is then added to the mesh
+// with one global atomic per non-zero node.  Particles whose stencil leaves the tile (only
+// possible through rounding at the cell faces) go straight to the mesh.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_deposit_cells(const double *__restrict__ pos, const uint32_t *__restrict__ cell_start,
+                    P3MGeom g, int W, T *__restrict__ mesh)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    const int M = g.mesh, nc = g.n_c, W3 = W * W * W;
+    const int64_t n = g.n;
+    for (int cell = blockIdx.x; cell < g.n_cells; cell += gridDim.x) {
+        const uint32_t s = cell_start[cell], e = cell_start[cell + 1];
+        if (s == e) continue;
+        const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+        const int ox = (int)((int64_t)cx * M / nc) - 1;
+        const int oy = (int)((int64_t)cy * M / nc) - 1;
+        const int oz = (int)((int64_t)cz * M / nc) - 1;
+        for (int t = threadIdx.x; t < W3; t += blockDim.x) tile[t] = T(0);
+        __syncthreads();
+        for (uint32_t k = s + threadIdx.x; k < e; k += blockDim.x) {
+            int ix, iy, iz;
+            T fx, fy, fz;
+            cic_stencil(pos[k], g.inv_h, ix, fx);
+            cic_stencil(pos[n + k], g.inv_h, iy, fy);
+            cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
+            const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+            const int lx = ix - ox, ly = iy - oy, lz = iz - oz;
+            if (lx >= 0 && lx + 1 < W && ly >= 0 && ly + 1 < W && lz >= 0 && lz + 1 < W) {
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const T wab = wx[a] * wy[b];
+                        T *row = tile + ((lx + a) * W + (ly + b)) * W + lz;
+                        atomicAdd(row, wab * wz[0]);
+                        atomicAdd(row + 1, wab * wz[1]);
+                    }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const size_t node = ((size_t)wrap_index(ix + a, M) * M +
+                                                 wrap_index(iy + b, M)) * M + wrap_index(iz + c, M);
+                            atomicAdd(mesh + node, wx[a] * wy[b] * wz[c]);
+                        }
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < W3; t += blockDim.x) {
+            const T v = tile[t];
+            if (v != T(0)) {
+                const int lz = t % W, ly = (t / W) % W, lx = t / (W * W);
+                const size_t node = ((size_t)wrap_index(ox + lx, M) * M + wrap_index(oy + ly, M)) * M +
+                                    wrap_index(oz + lz, M);
+                atomicAdd(mesh + node, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Fallback when a cell's node tile does not fit in shared memory: one global atomic per
+// stencil node.
+template <typename T>
+__global__ void k_deposit_direct(const double *__restrict__ pos, P3MGeom g, T *__restrict__ mesh)
+{
+    const int M = g.mesh;
+    const int64_t n = g.n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        T fx, fy, fz;
+        cic_stencil(pos[k], g.inv_h, ix, fx);
+        cic_stencil(pos[n + k], g.inv_h, iy, fy);
+        cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
+        const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const size_t node = ((size_t)wrap_index(ix + a, M) * M + wrap_index(iy + b, M)) * M +
+                                        wrap_index(iz + c, M);
+                    atomicAdd(mesh + node, wx[a] * wy[b] * wz[c]);
+                }
+    }
+}
+
+// Fused k-space pass: G(k) = C * t(kx) t(ky) t(kz) / k^2 with t the per-axis Gaussian filter
+// and deconvolution factor, then F_d = -i kg_d G rho_k for the three axes.
+template <typename T, typename C2>
+__global__ void __launch_bounds__(256)
+    k_kspace(const C2 *__restrict__ rho_k, const T *__restrict__ tk, const T *__restrict__ tkg,
+             const T *__restrict__ tg, int M, T gconst, C2 *__restrict__ fx,
+             C2 *__restrict__ fy, C2 *__restrict__ fz)
+{
+    const int nz = M / 2 + 1;
+    const size_t total = (size_t)M * M * nz;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int iz = (int)(idx % nz);
+        const size_t t = idx / nz;
+        const int iy = (int)(t % M), ix = (int)(t / M);
+        const T kx = tk[ix], ky = tk[iy], kz = tk[iz];
+        const T k2 = kx * kx + ky * ky + kz * kz;
+        const T G = idx == 0 ? T(0) : gconst * (tg[ix] * tg[iy] * tg[iz]) / k2;
+        const C2 r = rho_k[idx];
+        const T gx = G * tkg[ix], gy = G * tkg[iy], gz = G * tkg[iz];
+        C2 o;
+        o.x = gx * r.y;
+        o.y = -gx * r.x;
+        fx[idx] = o;
+        o.x = gy * r.y;
+        o.y = -gy * r.x;
+        fy[idx] = o;
+        o.x = gz * r.y;
+        o.y = -gz * r.x;
+        fz[idx] = o;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_gather(const double *__restrict__ pos, P3MGeom g, const T *__restrict__ fxm,
+             const T *__restrict__ fym, const T *__restrict__ fzm, double *__restrict__ acc)
+{
+    const int M = g.mesh;
+    const int64_t n = g.n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        T fx, fy, fz;
+        cic_stencil(pos[k], g.inv_h, ix, fx);
+        cic_stencil(pos[n + k], g.inv_h, iy, fy);
+        cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
+        const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+        const int jx[2] = {wrap_index(ix, M), wrap_index(ix + 1, M)};
+        const int jy[2] = {wrap_index(iy, M), wrap_index(iy + 1, M)};
+        const int jz[2] = {wrap_index(iz, M), wrap_index(iz + 1, M)};
+        T ax = 0, ay = 0, az = 0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const T w = wx[a] * wy[b] * wz[c];
+                    const size_t node = ((size_t)jx[a] * M + jy[b]) * M + jz[c];
+                    ax += w * __ldg(fxm + node);
+                    ay += w * __ldg(fym + node);
+                    az += w * __ldg(fzm + node);
+                }
+        acc[k] = (double)ax;
+        acc[n + k] = (double)ay;
+        acc[2 * n + k] = (double)az;
+    }
+}
+
+inline int grid_for(size_t n, int threads, int num_sms)
+{
+    size_t b = (n + threads - 1) / threads;
+    size_t cap = (size_t)num_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+cudaError_t deposit_impl(p3m_ctx *c)
+{
+    const size_t M3 = (size_t)c->g.mesh * c->g.mesh * c->g.mesh;
+    T *mesh = (T *)c->rho;
+    c->launches += 2;  // fill, deposit
+    k_fill<T><<<grid_for(M3, 256, c->num_sms), 256, 0, c->stream>>>(mesh, M3, (T)(-c->g.mean_count));
+    const int W = (c->g.mesh + c->g.n_c - 1) / c->g.n_c + 4;
+    const size_t smem = (size_t)W * W * W * sizeof(T);
+    if (smem <= 48 * 1024) {
+        const int grid = c->g.n_cells < c->num_sms * 8 ? c->g.n_cells : c->num_sms * 8;
+        k_deposit_cells<T><<<grid, 256, smem, c->stream>>>(c->pos, c->cell_start, c->g, W, mesh);
+    } else {
+        k_deposit_direct<T><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(c->pos, c->g,
+                                                                                       mesh);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_deposit(p3m_ctx *c)
+{
+    return c->precision == P3M_PREC_MIXED ? deposit_impl<float>(c) : deposit_impl<double>(c);
+}
+
+cudaError_t launch_kspace(p3m_ctx *c)
+{
+    const int M = c->g.mesh;
+    const size_t nk = (size_t)M * M * (M / 2 + 1);
+    const int grid = grid_for(nk, 256, c->num_sms);
+    c->launches += 1;
+    if (c->precision == P3M_PREC_MIXED) {
+        cufftComplex *f = (cufftComplex *)c->frc_k;
+        k_kspace<float, cufftComplex><<<grid, 256, 0, c->stream>>>(
+            (const cufftComplex *)c->rho_k, (const float *)c->tab_k, (const float *)c->tab_kg,
+            (const float *)c->tab_g, M, (float)c->green_const, f, f + nk, f + 2 * nk);
+    } else {
+        cufftDoubleComplex *f = (cufftDoubleComplex *)c->frc_k;
+        k_kspace<double, cufftDoubleComplex><<<grid, 256, 0, c->stream>>>(
+            (const cufftDoubleComplex *)c->rho_k, (const double *)c->tab_k,
+            (const double *)c->tab_kg, (const double *)c->tab_g, M, c->green_const, f, f + nk,
+            f + 2 * nk);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(p3m_ctx *c, double *acc_out)
+{
+    const size_t M3 = (size_t)c->g.mesh * c->g.mesh * c->g.mesh;
+    const int grid = grid_for(c->g.n, 256, c->num_sms);
+    c->launches += 1;
+    if (c->precision == P3M_PREC_MIXED) {
+        const float *f = (const float *)c->frc;
+        k_gather<float><<<grid, 256, 0, c->stream>>>(c->pos, c->g, f, f + M3, f + 2 * M3, acc_out);
+    } else {
+        const double *f = (const double *)c->frc;
+        k_gather<double><<<grid, 256, 0, c->stream>>>(c->pos, c->g, f, f + M3, f + 2 * M3, acc_out);
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,132 @@
+// Internal declarations of the P3M library: the context and the launchers of each phase.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include "p3m.h"
+
+// Chaining-cell geometry, mesh constants and the per-evaluation scalars every kernel needs.
+struct P3MGeom {
+    double box;       // L
+    int64_t n;        // N
+    int mesh;         // M
+    double inv_h;     // M / L
+    double r_s, r_c;  // split scale and cutoff (length)
+    double eps;       // Plummer softening (length)
+    double gm;        // G m
+    int n_c;          // chaining cells per side
+    int sub_bits;     // b
+    int n_fine;       // n_c << b
+    double inv_fine;  // n_fine / L
+    double cs;        // L / n_c
+    int n_cells;      // n_c^3
+    double mean_count;  // N / M^3
+};
+
+struct p3m_ctx {
+    P3MGeom g;
+    int precision;
+    int deconvolve;
+    int short_range;
+    p3m_cosmology cosmo;
+    double mass;
+    double a;
+    cudaStream_t stream;
+    int num_sms;
+
+    // particle state in sorted order, SoA [3][n]
+    double *pos, *mom, *acc, *acc_lr;
+    uint32_t *pid;
+    double *pos_alt, *mom_alt;  // permute targets / staging
+    uint32_t *pid_alt;
+    void *rel;  // float4 (mixed) or double4 (fp64): position relative to its cell origin
+
+    // sort
+    uint32_t *keys, *keys_alt, *vals, *vals_alt;
+    uint32_t *digit_counts;  // 256 * n_tiles
+    uint32_t *scan_aux;      // block sums of the scans
+    int n_tiles;
+    int key_bits;
+    uint32_t *cell_start;  // n_cells + 1
+    uint32_t *work;        // pair work items (cell, first slot)
+    uint32_t *work_off;    // n_cells + 1
+    size_t max_work;
+    uint32_t *counters;  // [0] work cursor [1] error flags [2] max cell count [3] spare
+    unsigned long long *pair_count;  // [0] last evaluation [1] cumulative
+    unsigned long long launches;     // kernels launched by the library (host-side count)
+    double *red;  // reduction partials
+
+    // mesh (float or double)
+    void *rho, *rho_k, *frc_k, *frc;
+    void *tab_k, *tab_kg, *tab_g;  // per-axis |k|, gradient k, Green factor (length M)
+    double green_const;
+    cufftHandle plan_r2c, plan_c2r;
+    bool plans_made;
+
+    // timing
+    bool timing;
+    cudaEvent_t *ev;
+    int *ev_phase;
+    int ev_used, ev_cap;
+    double phase_ms[P3M_NPHASES];
+
+    bool have_particles;
+    bool forces_valid;
+    bool sorted_valid;
+    char err[512];
+};
+
+enum {
+    PH_KICK_DRIFT = 0,
+    PH_SORT,
+    PH_PERMUTE,
+    PH_DEPOSIT,
+    PH_FFT_R2C,
+    PH_KSPACE,
+    PH_FFT_C2R,
+    PH_GATHER,
+    PH_PAIRS,
+    PH_OTHER
+};
+
+#define P3M_SORT_TILE 4096   // keys per radix-sort tile (256 threads x 16)
+#define P3M_PAIR_TI 128      // i-particles per pair work item (one per thread)
+#define P3M_PAIR_TJ 256      // j-particles per shared-memory tile
+#define P3M_FLAG_TIMEOUT 1u  // counters[1] bit: a bounded wait gave up
+#define P3M_FLAG_NONFINITE 2u
+
+// ------------------------------------------------------------------ launchers (sort.cu)
+// Wraps positions and writes keys (optionally after a kick with kfac = m K and a drift with
+// dfac = D / m).  vals are not touched.
+cudaError_t launch_kick_drift_keys(p3m_ctx *c, bool kick_drift, double kfac, double dfac);
+// Stable LSD radix sort of (keys, identity) -> c->keys (sorted), c->vals (source slots).
+cudaError_t launch_radix_sort(p3m_ctx *c);
+// Permutes pos/mom/pid by c->vals, writes the relative coordinates, cell_start, work list.
+cudaError_t launch_permute_and_cells(p3m_ctx *c);
+// Exclusive scan of n uint32 values (in may equal out); aux needs ceil(n/4096)+1 entries.
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *aux,
+                            cudaStream_t s);
+
+// ------------------------------------------------------------------ launchers (mesh.cu)
+cudaError_t launch_deposit(p3m_ctx *c);
+cudaError_t launch_kspace(p3m_ctx *c);
+cudaError_t launch_gather(p3m_ctx *c, double *acc_out);
+
+// ------------------------------------------------------------------ launchers (pair.cu)
+// acc_out = acc_in + SR (acc_in NULL: SR only); kfac != 0: mom += kfac * acc_out.
+cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac);
+
+// ------------------------------------------------------------------ launchers (integrate.cu)
+cudaError_t launch_kick(p3m_ctx *c, double kfac);
+// y += alpha x over 3n values
+cudaError_t launch_axpy(p3m_ctx *c, double *y, const double *x, double alpha);
+cudaError_t launch_load_particles(p3m_ctx *c, const double *pos, const double *mom,
+                                  const double *acc);
+cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst);
+cudaError_t launch_diag(p3m_ctx *c, double *host_out /* [4]: px py pz 2*kinetic*m*a^2 */);
+
+// host helpers (api.cu)
+double p3m_kick_factor(const p3m_cosmology &cs, double a1, double a2);
+double p3m_drift_factor(const p3m_cosmology &cs, double a1, double a2);

@@ -1,0 +1,409 @@
+// Chaining-cell keys, stable LSD radix sort, particle permutation, cell ranges and the
+// pair work list.
+//
+// Key of a particle (the chaining-mesh binning of P3M; the guide only fixes the cutoff that
+// sets the cell size, Ch. Parameters "P3M_cutoff"): with n_f = n_c 2^b fine cells per side,
+//   f_d = min(trunc(x_d * (n_f / L)), n_f - 1)   (one correctly rounded FP64 multiply)
+//   cell = (c_z n_c + c_y) n_c + c_x,  c_d = f_d >> b
+//   key  = (cell << 3b) | Morton(f_x mod 2^b, f_y mod 2^b, f_z mod 2^b)
+// Particles are ordered by key, ties by their current slot (a stable sort), so the order is
+// reproducible bit for bit.
+#include <cuda_runtime.h>
+
+#include "p3m_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = P3M_SORT_TILE / kThreads;  // 16
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+__device__ __forceinline__ double wrap_box(double x, double L)
+{
+    x = fmod(x, L);
+    if (x < 0.0) x = __dadd_rn(x, L);
+    if (x >= L) x = __dadd_rn(x, -L);
+    return x;
+}
+
+__device__ __forceinline__ uint32_t fine_index(double x, double inv, int nf)
+{
+    int f = (int)__dmul_rn(x, inv);  // x >= 0: truncation is floor
+    return (uint32_t)min(f, nf - 1);
+}
+
+__device__ __forceinline__ uint32_t make_key(uint32_t fx, uint32_t fy, uint32_t fz,
+                                             const P3MGeom &g)
+{
+    const int b = g.sub_bits;
+    const uint32_t cell = ((fz >> b) * (uint32_t)g.n_c + (fy >> b)) * (uint32_t)g.n_c + (fx >> b);
+    const uint32_t m = (1u << b) - 1u;
+    uint32_t sx = fx & m, sy = fy & m, sz = fz & m, code = 0;
+    for (int t = 0; t < b; ++t)
+        code |= (((sx >> t) & 1u) << (3 * t)) | (((sy >> t) & 1u) << (3 * t + 1)) |
+                (((sz >> t) & 1u) << (3 * t + 2));
+    return (cell << (3 * b)) | code;
+}
+
+// Half kick + drift (optional), periodic wrap, key.  Kick and drift use separately rounded
+// products and sums: p += (m K) a; x += p (D / m).
+__global__ void k_kick_drift_keys(double *__restrict__ pos, double *__restrict__ mom,
+                                  const double *__restrict__ acc, P3MGeom g, int kick_drift,
+                                  double kfac, double dfac, uint32_t *__restrict__ keys)
+{
+    const int64_t n = g.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t f[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double x = pos[d * n + i];
+            if (kick_drift) {
+                double p = __dadd_rn(mom[d * n + i], __dmul_rn(kfac, acc[d * n + i]));
+                mom[d * n + i] = p;
+                x = __dadd_rn(x, __dmul_rn(p, dfac));
+            }
+            x = wrap_box(x, g.box);
+            pos[d * n + i] = x;
+            f[d] = fine_index(x, g.inv_fine, g.n_fine);
+        }
+        keys[i] = make_key(f[0], f[1], f[2], g);
+    }
+}
+
+// ------------------------------------------------------------------ radix sort, 8-bit digits
+// Tile t holds keys [t*4096, (t+1)*4096), visited in 16 rounds of 256 consecutive keys;
+// within a round warp w holds keys [w*32, w*32+32).  That visiting order is the input order,
+// so ranks assigned round by round, warp by warp, lane by lane make each pass stable.
+
+__global__ void __launch_bounds__(kThreads)
+    k_radix_upsweep(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                    uint32_t *__restrict__ counts, int n_tiles)
+{
+    __shared__ uint32_t hist[kRadix];
+    const int tid = threadIdx.x, lane = tid & 31;
+    hist[tid] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * P3M_SORT_TILE;
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t idx = base + r * kThreads + tid;
+        const bool valid = idx < n;
+        const uint32_t d = valid ? (keys[idx] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    counts[(size_t)tid * n_tiles + blockIdx.x] = hist[tid];
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                      int64_t n, int shift, const uint32_t *__restrict__ offsets, int n_tiles,
+                      uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out)
+{
+    __shared__ uint32_t s_base[kRadix];
+    __shared__ uint32_t s_cnt[kThreads / 32][kRadix];
+    __shared__ uint32_t s_pos[kThreads / 32][kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_base[tid] = offsets[(size_t)tid * n_tiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s_cnt[w][tid] = 0;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * P3M_SORT_TILE;
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t idx = base + r * kThreads + tid;
+        const bool valid = idx < n;
+        uint32_t key = 0, val = 0;
+        if (valid) {
+            key = keys_in[idx];
+            val = vals_in ? vals_in[idx] : (uint32_t)idx;
+        }
+        const uint32_t d = valid ? (key >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) s_cnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = s_base[tid];
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const uint32_t c = s_cnt[w][tid];
+                s_cnt[w][tid] = 0;
+                s_pos[w][tid] = run;
+                run += c;
+            }
+            s_base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t p = s_pos[warp][d] + rank;
+            keys_out[p] = key;
+            vals_out[p] = val;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ exclusive scan (uint32)
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t warp_sums[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = lane < kThreads / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = warp ? warp_sums[warp - 1] : 0u;
+    if (total) *total = warp_sums[kThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_scan_reduce(const uint32_t *__restrict__ in, size_t n, uint32_t *__restrict__ aux)
+{
+    const size_t base = (size_t)blockIdx.x * P3M_SORT_TILE;
+    uint32_t s = 0;
+    for (int r = 0; r < kItems; ++r) {
+        const size_t i = base + r * kThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    uint32_t total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) aux[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of aux[0..nb) in place, aux[nb] = total.
+__global__ void __launch_bounds__(kThreads) k_scan_aux(uint32_t *aux, size_t nb)
+{
+    uint32_t carry = 0;
+    for (size_t base = 0; base < nb; base += kThreads) {
+        const size_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? aux[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, &total);
+        if (i < nb) aux[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) aux[nb] = carry;
+}
+
+// Each thread owns 16 consecutive items of the block's 4096 (read before any write, so
+// in == out is allowed).
+__global__ void __launch_bounds__(kThreads)
+    k_scan_down(const uint32_t *in, uint32_t *out, size_t n, const uint32_t *__restrict__ aux)
+{
+    const size_t base = (size_t)blockIdx.x * P3M_SORT_TILE + (size_t)threadIdx.x * kItems;
+    uint32_t v[kItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        v[r] = (base + r < n) ? in[base + r] : 0u;
+        s += v[r];
+    }
+    uint32_t run = aux[blockIdx.x] + block_exclusive_scan(s, nullptr);
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        if (base + r < n) out[base + r] = run;
+        run += v[r];
+    }
+}
+
+// ------------------------------------------------------------------ permutation and cells
+
+template <typename R4>
+__device__ __forceinline__ R4 make_rel(double x, double y, double z);
+template <>
+__device__ __forceinline__ float4 make_rel<float4>(double x, double y, double z)
+{
+    return make_float4((float)x, (float)y, (float)z, 0.0f);
+}
+template <>
+__device__ __forceinline__ double4 make_rel<double4>(double x, double y, double z)
+{
+    return make_double4(x, y, z, 0.0);
+}
+
+template <typename R4>
+__global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys,
+                          P3MGeom g, const double *__restrict__ pos,
+                          const double *__restrict__ mom, const uint32_t *__restrict__ pid,
+                          double *__restrict__ pos_out, double *__restrict__ mom_out,
+                          uint32_t *__restrict__ pid_out, R4 *__restrict__ rel)
+{
+    const int64_t n = g.n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[k];
+        const double x = pos[j], y = pos[n + j], z = pos[2 * n + j];
+        pos_out[k] = x;
+        pos_out[n + k] = y;
+        pos_out[2 * n + k] = z;
+        mom_out[k] = mom[j];
+        mom_out[n + k] = mom[n + j];
+        mom_out[2 * n + k] = mom[2 * n + j];
+        pid_out[k] = pid[j];
+        const uint32_t cell = keys[k] >> (3 * g.sub_bits);
+        const uint32_t cx = cell % g.n_c, cy = (cell / g.n_c) % g.n_c, cz = cell / (g.n_c * g.n_c);
+        rel[k] = make_rel<R4>(x - (double)cx * g.cs, y - (double)cy * g.cs, z - (double)cz * g.cs);
+    }
+}
+
+// cell_start[c] = first sorted slot whose cell is >= c (slots k = 0..n, cell(n) = n_cells).
+__global__ void k_cell_start(const uint32_t *__restrict__ keys, P3MGeom g,
+                             uint32_t *__restrict__ cell_start)
+{
+    const int64_t n = g.n;
+    const int sh = 3 * g.sub_bits;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t prev = k > 0 ? (int64_t)(keys[k - 1] >> sh) : -1;
+        const int64_t cur = k < n ? (int64_t)(keys[k] >> sh) : (int64_t)g.n_cells;
+        for (int64_t c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)k;
+    }
+}
+
+__global__ void k_work_count(const uint32_t *__restrict__ cell_start, int n_cells,
+                             uint32_t *__restrict__ work_n, uint32_t *__restrict__ max_count)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
+        const uint32_t cnt = cell_start[c + 1] - cell_start[c];
+        work_n[c] = (cnt + P3M_PAIR_TI - 1) / P3M_PAIR_TI;
+        if (cnt) atomicMax(max_count, cnt);
+    }
+}
+
+// Work item = (cell << 0, first slot) packed as two uint32: work[2w] = cell, work[2w+1] = slot.
+__global__ void k_work_fill(const uint32_t *__restrict__ cell_start,
+                            const uint32_t *__restrict__ work_off, int n_cells,
+                            uint32_t *__restrict__ work)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
+        const uint32_t s = cell_start[c], e = cell_start[c + 1];
+        uint32_t w = work_off[c];
+        for (uint32_t i = s; i < e; i += P3M_PAIR_TI, ++w) {
+            work[2 * (size_t)w] = (uint32_t)c;
+            work[2 * (size_t)w + 1] = i;
+        }
+    }
+}
+
+inline int grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_kick_drift_keys(p3m_ctx *c, bool kick_drift, double kfac, double dfac)
+{
+    c->launches += 1;
+    k_kick_drift_keys<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+        c->pos, c->mom, c->acc, c->g, kick_drift ? 1 : 0, kfac, dfac, c->keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *aux,
+                            cudaStream_t s)
+{
+    const size_t nb = (n + P3M_SORT_TILE - 1) / P3M_SORT_TILE;
+    if (nb == 0) return cudaSuccess;
+    k_scan_reduce<<<(unsigned)nb, kThreads, 0, s>>>(in, n, aux);
+    k_scan_aux<<<1, kThreads, 0, s>>>(aux, nb);
+    k_scan_down<<<(unsigned)nb, kThreads, 0, s>>>(in, out, n, aux);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radix_sort(p3m_ctx *c)
+{
+    const int64_t n = c->g.n;
+    const int passes = (c->key_bits + kRadixBits - 1) / kRadixBits;
+    const size_t ncount = (size_t)kRadix * c->n_tiles;
+    uint32_t *kin = c->keys, *kout = c->keys_alt;
+    uint32_t *vin = nullptr, *vout = c->vals;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        c->launches += 5;  // upsweep, 3 scan kernels, downsweep
+        k_radix_upsweep<<<c->n_tiles, kThreads, 0, c->stream>>>(kin, n, shift, c->digit_counts,
+                                                                c->n_tiles);
+        cudaError_t e = launch_scan_u32(c->digit_counts, c->digit_counts, ncount, c->scan_aux,
+                                        c->stream);
+        if (e != cudaSuccess) return e;
+        k_radix_downsweep<<<c->n_tiles, kThreads, 0, c->stream>>>(
+            kin, vin, n, shift, c->digit_counts, c->n_tiles, kout, vout);
+        // next pass reads what this one wrote
+        uint32_t *t = kin;
+        kin = kout;
+        kout = t;
+        vin = vout;
+        vout = (vout == c->vals) ? c->vals_alt : c->vals;
+    }
+    // make c->keys / c->vals the sorted result
+    if (kin != c->keys) {
+        uint32_t *t = c->keys;
+        c->keys = kin;
+        c->keys_alt = t;
+    }
+    if (vin != c->vals) {
+        uint32_t *t = c->vals;
+        c->vals = vin;
+        c->vals_alt = t;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_and_cells(p3m_ctx *c)
+{
+    const int64_t n = c->g.n;
+    const int gb = grid_for(n, 256, c->num_sms);
+    c->launches += 7;  // permute, cell_start, work_count, 3 scan kernels, work_fill
+    if (c->precision == P3M_PREC_MIXED)
+        k_permute<float4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
+                                                     c->pid, c->pos_alt, c->mom_alt, c->pid_alt,
+                                                     (float4 *)c->rel);
+    else
+        k_permute<double4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
+                                                      c->pid, c->pos_alt, c->mom_alt,
+                                                      c->pid_alt, (double4 *)c->rel);
+    double *t = c->pos;
+    c->pos = c->pos_alt;
+    c->pos_alt = t;
+    t = c->mom;
+    c->mom = c->mom_alt;
+    c->mom_alt = t;
+    uint32_t *u = c->pid;
+    c->pid = c->pid_alt;
+    c->pid_alt = u;
+
+    k_cell_start<<<grid_for(n + 1, 256, c->num_sms), 256, 0, c->stream>>>(c->keys, c->g,
+                                                                         c->cell_start);
+    cudaMemsetAsync(c->counters + 2, 0, sizeof(uint32_t), c->stream);
+    const int gc = grid_for(c->g.n_cells, 256, c->num_sms);
+    cudaMemsetAsync(c->work_off + c->g.n_cells, 0, sizeof(uint32_t), c->stream);
+    k_work_count<<<gc, 256, 0, c->stream>>>(c->cell_start, c->g.n_cells, c->work_off,
+                                            c->counters + 2);
+    cudaError_t e = launch_scan_u32(c->work_off, c->work_off, (size_t)c->g.n_cells + 1,
+                                    c->scan_aux, c->stream);
+    if (e != cudaSuccess) return e;
+    k_work_fill<<<gc, 256, 0, c->stream>>>(c->cell_start, c->work_off, c->g.n_cells, c->work);
+    return cudaGetLastError();
+}

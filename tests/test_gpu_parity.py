@@ -1,0 +1,266 @@
+"""GPU parity of the P3M step (through the C ABI) against the FP64 oracle.
+
+Acceptance bars:
+  * cell keys, sort order and cell ranges: bit-exact;
+  * accelerations: relative RMS sqrt(sum|a_gpu - a_ref|^2 / sum|a_ref|^2) <= 1e-5 in the mixed
+    (FP32 force) mode and <= 1e-12 in the all-FP64 mode;
+  * positions after 10 KDK steps: within 1e-6 of the box length (mixed mode).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import p3m_synth as S
+from oracle import p3m_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"mixed": 1e-5, "fp64": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def P3M():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_07621_gb300 import build
+    build.build()
+    from paper_1510_07621_gb300 import P3M as cls
+    return cls
+
+
+def rel_rms(a, ref):
+    return math.sqrt(float(np.sum((a - ref) ** 2)) / float(np.sum(ref ** 2)))
+
+
+def _case(name):
+    if name == "eds32":  # 32^3 Zel'dovich ICs at a = 0.02, box 64 Mpc/h, mesh 32
+        pos, mom = S.zeldovich(32, 64.0, 0.02, 1511)
+        return pos, mom, dict(box=64.0, mesh=32)
+    if name == "clustered48":  # uneven cell occupancy: dense halos and empty cells
+        pos, mom = S.clustered(48, 100.0, 4001)
+        return pos, mom, dict(box=100.0, mesh=48)
+    if name == "random5003":  # N not a cube, ragged tiles everywhere
+        pos = S.uniform_random(5003, 80.0, 77)
+        return pos, np.zeros_like(pos), dict(box=80.0, mesh=40)
+    if name == "tiny3":
+        pos = np.array([[1.0, 1.5, 30.0], [2.0, 2.0, 31.0], [3.0, 3.3, 0.5]])
+        return pos, np.zeros_like(pos), dict(box=32.0, mesh=32)
+    raise KeyError(name)
+
+
+def _params(n, kw, precision="mixed", **extra):
+    soft = extra.pop("softening", 0.02)
+    return O.Params(kw["box"], n, kw["mesh"], softening=soft, **extra)
+
+
+# ------------------------------------------------------------------ keys and order
+
+
+def _adversarial(box=64.0, mesh=32):
+    """Edge positions: all particles in one cell, exact cell faces, L - ulp, out-of-box."""
+    p = O.Params(box, 10, mesh)
+    cs = box / p.n_c
+    xs = [0.0, cs, 2 * cs, 3 * cs, np.nextafter(cs, 0), np.nextafter(box, 0), -1e-300, box,
+          -0.25 * box, 2.5 * box, 0.5 * cs, 0.5 * cs, 0.5 * cs, 0.5 * cs]
+    u = S.uniform01(5, 3 * 400)
+    one_cell = (u.reshape(3, 400) * 0.9 + 0.05) * cs + cs  # all in cell (1,1,1)
+    edge = np.array([[x, y, z] for x in xs[:6] for y in xs[4:10] for z in xs[8:]]).T
+    return np.concatenate([one_cell, edge], axis=1), dict(box=box, mesh=mesh)
+
+
+@pytest.mark.parametrize("sub_bits", [0, 2])
+@pytest.mark.parametrize("case", ["eds32", "clustered48", "adversarial"])
+def test_keys_order_and_cell_ranges_bit_exact(P3M, case, sub_bits):
+    if case == "adversarial":
+        pos, kw = _adversarial()
+        mom = np.zeros_like(pos)
+    else:
+        pos, mom, kw = _case(case)
+    n = pos.shape[1]
+    with P3M(kw["box"], n, kw["mesh"], sub_bits=sub_bits) as sim:
+        sim.set_particles(np.ascontiguousarray(pos), np.ascontiguousarray(mom), a=0.1)
+        sim.forces(0.1)
+        keys, ids, starts = sim.get_cells()
+    p = O.Params(kw["box"], n, kw["mesh"], sub_bits=sub_bits)
+    x = O.wrap(pos, kw["box"])
+    cell, key = O.cell_keys(x, p)
+    order = O.stable_order(key)
+    assert np.array_equal(keys.astype(np.int64), key[order])
+    assert np.array_equal(ids.astype(np.int64), order)
+    assert np.array_equal(starts.astype(np.int64), O.cell_start(cell[order], p.n_c ** 3))
+
+
+def test_positions_wrapped_and_order_preserved(P3M):
+    pos, _ = _adversarial()
+    n = pos.shape[1]
+    mom = S.uniform01(9, 3 * n).reshape(3, n)
+    with P3M(64.0, n, 32) as sim:
+        sim.set_particles(np.ascontiguousarray(pos), mom, a=0.5)
+        sim.forces(0.5)
+        p2, m2 = sim.get_particles()
+    assert np.array_equal(p2, O.wrap(pos, 64.0))
+    assert np.array_equal(m2, mom)
+
+
+# ------------------------------------------------------------------ mesh and forces
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_density_mesh(P3M, precision):
+    pos, mom, kw = _case("clustered48")
+    n = pos.shape[1]
+    with P3M(kw["box"], n, kw["mesh"], precision=precision) as sim:
+        sim.set_particles(pos, mom, a=1.0)
+        sim.forces(1.0)
+        rho = sim.get_mesh(0).astype(np.float64)
+    ref = O.cic_deposit(O.wrap(pos, kw["box"]), _params(n, kw)) - n / kw["mesh"] ** 3
+    tol = 2e-5 if precision == "mixed" else 1e-12
+    assert np.max(np.abs(rho - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("case", ["eds32", "clustered48", "random5003", "tiny3"])
+def test_force_parts_match_oracle(P3M, case, precision):
+    pos, mom, kw = _case(case)
+    n = pos.shape[1]
+    with P3M(kw["box"], n, kw["mesh"], precision=precision) as sim:
+        sim.set_particles(pos, mom, a=1.0)
+        lr, sr = sim.forces_split()
+        diag = sim.diagnostics()
+        tot = sim.forces(1.0)
+    p = _params(n, kw)
+    x = O.wrap(pos, kw["box"])
+    lr_ref = O.pm_accel(x, p)
+    sr_ref, npairs = O.sr_accel(x, p)
+    tol = TOL[precision]
+    assert rel_rms(lr, lr_ref) <= tol
+    if npairs:
+        assert rel_rms(sr, sr_ref) <= tol
+    else:
+        assert np.max(np.abs(sr)) == 0.0
+    assert rel_rms(tot, lr_ref + sr_ref) <= tol
+    # pairs within FP32 rounding of r = r_c may fall on either side in the mixed mode
+    slack = 0 if precision == "fp64" else max(2, int(2e-5 * npairs))
+    assert abs(diag["pairs"] - npairs) <= slack
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_pure_pm_mode(P3M, precision):
+    pos, mom, kw = _case("eds32")
+    n = pos.shape[1]
+    with P3M(kw["box"], n, kw["mesh"], precision=precision, short_range=False) as sim:
+        sim.set_particles(pos, mom, a=0.02)
+        acc = sim.forces(0.02)
+    ref = O.pm_accel(O.wrap(pos, kw["box"]), _params(n, kw, short_range=False))
+    assert rel_rms(acc, ref) <= TOL[precision]
+
+
+def test_momentum_conservation(P3M):
+    pos, mom, kw = _case("clustered48")
+    n = pos.shape[1]
+    with P3M(kw["box"], n, kw["mesh"], precision="fp64") as sim:
+        sim.set_particles(pos, mom, a=1.0)
+        lr, sr = sim.forces_split()
+    for a in (lr, sr):
+        assert np.max(np.abs(a.sum(axis=1))) < 1e-11 * np.abs(a).sum()
+
+
+# ------------------------------------------------------------------ time stepping
+
+
+@pytest.mark.parametrize("precision,tol,mtol", [("mixed", 1e-6, 1e-4), ("fp64", 1e-11, 1e-9)])
+def test_ten_steps_eds32(P3M, precision, tol, mtol):
+    """Config of the 32^3 EdS run: 10 log-spaced steps a = 0.02 -> 0.1."""
+    pos, mom, kw = _case("eds32")
+    n = pos.shape[1]
+    a_s = S.log_spaced_steps(0.02, 0.1, 10)
+    with P3M(kw["box"], n, kw["mesh"], precision=precision) as sim:
+        sim.set_particles(pos, mom, a=a_s[0])
+        for i in range(10):
+            sim.step(a_s[i], a_s[i + 1] - a_s[i])
+        gpos, gmom = sim.get_particles()
+        d = sim.diagnostics()
+    p = _params(n, kw)
+    x, m = O.wrap(pos, kw["box"]), mom.copy()
+    acc = O.accel(x, p)
+    for i in range(10):
+        x, m, acc = O.step(x, m, acc, a_s[i], a_s[i + 1] - a_s[i], p)
+    dx = gpos - x
+    dx -= kw["box"] * np.round(dx / kw["box"])
+    assert np.max(np.abs(dx)) <= tol * kw["box"]
+    assert np.max(np.abs(gmom - m)) <= mtol * np.max(np.abs(m))
+    # the reductions of the diagnostics against numpy sums of the returned momenta
+    assert np.allclose(d["momentum"], gmom.sum(axis=1), rtol=0, atol=1e-12 * np.abs(gmom).sum())
+    assert abs(d["kinetic"] - O.kinetic_energy(gmom, a_s[-1])) <= 1e-12 * d["kinetic"]
+    assert abs(d["kinetic"] - O.kinetic_energy(m, a_s[-1])) <= mtol * d["kinetic"]
+
+
+def test_step_with_supplied_forces_equals_recompute(P3M):
+    """A state loaded with its accelerations steps exactly like one that recomputes them."""
+    pos, mom, kw = _case("eds32")
+    n = pos.shape[1]
+    with P3M(kw["box"], n, kw["mesh"]) as sim:
+        sim.set_particles(pos, mom, a=0.05)
+        acc = sim.forces(0.05)
+        sim.step(0.05, 0.01)
+        p1, m1 = sim.get_particles()
+        sim.set_particles(pos, mom, acc=acc, a=0.05)
+        sim.step(0.05, 0.01)
+        p2, m2 = sim.get_particles()
+    assert np.array_equal(p1, p2) and np.array_equal(m1, m2)
+
+
+# ------------------------------------------------------------------ errors
+
+
+def test_error_paths(P3M):
+    from paper_1510_07621_gb300 import P3MError, _lib
+    pos, mom, kw = _case("tiny3")
+    with P3M(kw["box"], 3, kw["mesh"]) as sim:
+        with pytest.raises(P3MError) as e:
+            sim.step(0.1, 0.01)
+        assert e.value.code == _lib.P3M_ESTATE
+        bad = pos.copy()
+        bad[1, 2] = np.nan
+        with pytest.raises(P3MError) as e:
+            sim.set_particles(bad, mom, a=0.1)
+        assert e.value.code == _lib.P3M_ENONFINITE
+        sim.set_particles(pos, mom, a=0.1)
+        with pytest.raises(P3MError) as e:
+            sim.step(0.1, -0.01)
+        assert e.value.code == _lib.P3M_EINVAL
+        sim.step(0.1, 0.01)
+
+
+# ------------------------------------------------------------------ full sizes, sampled
+
+
+def _sampled(P3M, pos, mom, box, mesh, n_sample, seed, a):
+    n = pos.shape[1]
+    with P3M(box, n, mesh) as sim:  # the launch configuration of the benchmark
+        sim.set_particles(pos, mom, a=a)
+        acc = sim.forces(a)
+        d = sim.diagnostics()
+    tg = np.unique((S.uniform01(seed, n_sample) * n).astype(np.int64) % n)
+    p = O.Params(box, n, mesh, softening=0.02)
+    ref = O.accel(O.wrap(pos, box), p, targets=tg)
+    return rel_rms(acc[:, tg], ref), d
+
+
+def test_full_size_clustered_128_sampled(P3M):
+    """128^3 particles, 128^3 mesh, box 200 Mpc/h, clustered late-time stand-in snapshot."""
+    pos, mom = S.clustered(128, 200.0, 1512)
+    err, d = _sampled(P3M, pos, mom, 200.0, 128, 400, 31, 1.0)
+    assert err <= TOL["mixed"], err
+    assert d["max_cell_count"] > 10 * (128 ** 3 // 22 ** 3)  # the input really is clustered
+
+
+@pytest.mark.slow
+def test_full_size_512_sampled(P3M):
+    """512^3 particles, 512^3 mesh, box 1000 Mpc/h, Zel'dovich ICs at a = 0.5."""
+    pos, mom = S.zeldovich(512, 1000.0, 0.5, 1513)
+    err, _ = _sampled(P3M, pos, mom, 1000.0, 512, 200, 32, 0.5)
+    assert err <= TOL["mixed"], err
