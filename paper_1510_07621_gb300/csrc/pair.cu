@@ -124,6 +124,9 @@ __global__ void __launch_bounds__(kTI)
             unsigned long long *__restrict__ pair_count)
 {
     using V4 = typename Vec4<T>::type;
+    // FP64 mode keeps absolute coordinates (d = (x_j - x_i) + image, the same operations as a
+    // plain minimum-image difference); FP32 mode uses cell-relative coordinates.
+    constexpr bool kAbsolute = sizeof(T) == 8;
     __shared__ __align__(128) V4 sj[2][kTJ];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ Neighbour nbr[27];
@@ -164,9 +167,18 @@ __global__ void __launch_bounds__(kTI)
             q.start = cell_start[nb];
             q.end = cell_start[nb + 1];
             const double L = g.box, cs = g.cs;
-            q.sx = ((double)wx * cs + (ux < 0 ? -L : (ux >= nc ? L : 0.0))) - (double)cx * cs;
-            q.sy = ((double)wy * cs + (uy < 0 ? -L : (uy >= nc ? L : 0.0))) - (double)cy * cs;
-            q.sz = ((double)wz * cs + (uz < 0 ? -L : (uz >= nc ? L : 0.0))) - (double)cz * cs;
+            const double ix = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+            const double iy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+            const double iz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            if (kAbsolute) {  // periodic image only
+                q.sx = ix;
+                q.sy = iy;
+                q.sz = iz;
+            } else {  // offset between the two cell origins (image included)
+                q.sx = ((double)wx * cs + ix) - (double)cx * cs;
+                q.sy = ((double)wy * cs + iy) - (double)cy * cs;
+                q.sz = ((double)wz * cs + iz) - (double)cz * cs;
+            }
             nbr[tid] = q;
         }
         __syncthreads();
@@ -213,15 +225,24 @@ __global__ void __launch_bounds__(kTI)
                 }
                 break;
             }
-            const T xs = (T)((double)xi.x - nbr[nb_c].sx);
-            const T ys = (T)((double)xi.y - nbr[nb_c].sy);
-            const T zs = (T)((double)xi.z - nbr[nb_c].sz);
+            // FP32: xs = x_i - shift, d = x_j - xs;  FP64: d = (x_j - x_i) + image
+            const T xs = kAbsolute ? (T)xi.x : (T)((double)xi.x - nbr[nb_c].sx);
+            const T ys = kAbsolute ? (T)xi.y : (T)((double)xi.y - nbr[nb_c].sy);
+            const T zs = kAbsolute ? (T)xi.z : (T)((double)xi.z - nbr[nb_c].sz);
+            const T ix = kAbsolute ? (T)nbr[nb_c].sx : T(0);
+            const T iy = kAbsolute ? (T)nbr[nb_c].sy : T(0);
+            const T iz = kAbsolute ? (T)nbr[nb_c].sz : T(0);
             T px = 0, py = 0, pz = 0;
             uint32_t cnt = 0;
             const V4 *tile = sj[buf];
             for (uint32_t j = 0; j < len; ++j) {
                 const V4 q = tile[j];
-                const T dx = q.x - xs, dy = q.y - ys, dz = q.z - zs;
+                T dx = q.x - xs, dy = q.y - ys, dz = q.z - zs;
+                if (kAbsolute) {
+                    dx += ix;
+                    dy += iy;
+                    dz += iz;
+                }
                 const T r2 = dx * dx + dy * dy + dz * dz;
                 if (r2 < rc2 && r2 > T(0)) {
                     const T f = pair_factor(r2, eps2, inv_rs);

@@ -240,6 +240,22 @@ __device__ __forceinline__ double4 make_rel<double4>(double x, double y, double 
     return make_double4(x, y, z, 0.0);
 }
 
+// FP32 mode: position minus its cell origin (no FP32 absolute coordinate).  FP64 mode: the
+// absolute position itself, so that the pair kernel forms x_j - x_i exactly like a plain
+// minimum-image difference.
+template <typename R4>
+__device__ __forceinline__ R4 rel_coords(double x, double y, double z, uint32_t cx, uint32_t cy,
+                                         uint32_t cz, double cs)
+{
+    return make_rel<R4>(x - (double)cx * cs, y - (double)cy * cs, z - (double)cz * cs);
+}
+template <>
+__device__ __forceinline__ double4 rel_coords<double4>(double x, double y, double z, uint32_t,
+                                                       uint32_t, uint32_t, double)
+{
+    return make_double4(x, y, z, 0.0);
+}
+
 template <typename R4>
 __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys,
                           P3MGeom g, const double *__restrict__ pos,
@@ -261,7 +277,7 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
         pid_out[k] = pid[j];
         const uint32_t cell = keys[k] >> (3 * g.sub_bits);
         const uint32_t cx = cell % g.n_c, cy = (cell / g.n_c) % g.n_c, cz = cell / (g.n_c * g.n_c);
-        rel[k] = make_rel<R4>(x - (double)cx * g.cs, y - (double)cy * g.cs, z - (double)cz * g.cs);
+        rel[k] = rel_coords<R4>(x, y, z, cx, cy, cz, g.cs);
     }
 }
 
