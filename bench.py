@@ -39,9 +39,12 @@ import p3m_synth as S  # noqa: E402
 
 METRIC = "P3M particle-updates/s"
 UNIT = "particle-updates/s"
-# algorithmic FP32 operations per accepted pair of the short-range sum (FMA = 2, each of
-# rsqrt/sqrt/exp/erfc = 1): d 3, r^2 5, +eps^2 1, 1/s 1, 1/s^3 2, r 1, x 1, g 8, f 1, a += 6
-FLOPS_PER_PAIR = 29
+# algorithmic FP32 flops per accepted pair of the short-range sum: the FP32 arithmetic of the
+# accepted-pair instruction sequence, FMA = 2: d 3 FADD; r^2 FMUL + 2 FFMA; r = r^2 rsqrt(r^2)
+# FMUL; r^3 FMUL; tau FFMA; Q(tau) 10 FFMA; g = 1 + r^3 Q FFMA; r^2 + eps^2 FADD;
+# g (r^2+eps^2)^-3/2 3 FMUL; a += f d 3 FFMA  ->  17 FFMA + 10 FADD/FMUL = 44 flops
+# (the two rsqrt run on the MUFU pipe and are not counted)
+FLOPS_PER_PAIR = 44
 WORKLOAD = dict(n_p=128, mesh=128, box=200.0, r_s_cells=1.25, cutoff=4.5, softening=0.02,
                 a_begin=0.02, a_end=1.0, setup_steps=64, seed=1512)
 WORKLOAD_NAME = ("clustered_128: 128^3 particles, 128^3 mesh, box 200 Mpc/h, r_s 1.25 cells, "
@@ -234,8 +237,14 @@ def run_ours(args, rank, world, local_rank, dist):
         per = ms / K
         entry = {"ms_per_launch": per, "share": ms / sum(phases.values())}
         if name == "pairs":
+            wj = [(b - a) / K for a, b in zip(d0["pair_warp_j"], d1["pair_warp_j"])]
+            slots = 32.0 * (wj[0] + wj[2])
             entry.update(bound="alu", achieved=pairs_per_step * FLOPS_PER_PAIR / (per / 1e3) / 1e12,
-                         peak=alu_peak, unit="TFLOP/s", pairs_per_launch=pairs_per_step)
+                         peak=alu_peak, unit="TFLOP/s", pairs_per_launch=pairs_per_step,
+                         flops_per_pair=FLOPS_PER_PAIR,
+                         warp_j_per_launch={"inside_chunks": wj[0], "tested": wj[1],
+                                            "tested_accepted": wj[2]},
+                         accepted_per_evaluated_slot=pairs_per_step / slots if slots else None)
         elif name in algo_bytes:
             entry.update(bound="hbm", achieved=algo_bytes[name] / (per / 1e3) / 1e9,
                          peak=hbm_peak, unit="GB/s")

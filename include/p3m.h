@@ -93,6 +93,10 @@ typedef struct {
     uint64_t pairs_total; /* the same, summed over every force evaluation of the context   */
     uint64_t launches;    /* kernels this library launched on the stream since p3m_init
                              (cuFFT's own kernels not included)                             */
+    uint64_t pair_warp_j[3]; /* pair kernel work since p3m_init, in warp-iterations over one
+                             j particle (32 pair slots each): [0] in chunks entirely inside
+                             r_c of every i of the warp, [1] in chunks tested pair by pair,
+                             [2] tested ones that some i accepted                          */
     int64_t n;            /* number of particles                                            */
     int32_t n_cells_side; /* chaining cells per side n_c                                    */
     int32_t max_cell_count; /* most particles in one chaining cell (last sort)              */
@@ -104,7 +108,7 @@ int p3m_default_options(p3m_options *opt);
 /*
  * Creates a context for n particles in a periodic box.
  *   box            side of the comoving box (Ch. Parameters, "boxsize"), > 0
- *   n              number of particles, 1 <= n < 2^32
+ *   n              number of particles, 1 <= n < 2^31
  *   mesh           PM_gridsize M: even, 8 <= M <= 2048
  *   r_s_cells      PM_scale: split scale r_s in mesh cells (> 0)
  *   cutoff_in_rs   P3M_cutoff: r_c = cutoff_in_rs * r_s (> 0); with short_range the box must

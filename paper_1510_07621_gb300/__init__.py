@@ -164,7 +164,8 @@ class P3M:
         self._check(self._lib.p3m_diagnostics(self._ctx, ctypes.byref(d)))
         return {"momentum": np.array(d.momentum[:]), "kinetic": d.kinetic, "a": d.a,
                 "pairs": int(d.pairs), "pairs_total": int(d.pairs_total),
-                "launches": int(d.launches), "n": int(d.n), "n_cells_side": int(d.n_cells_side),
+                "launches": int(d.launches), "pair_warp_j": [int(v) for v in d.pair_warp_j],
+                "n": int(d.n), "n_cells_side": int(d.n_cells_side),
                 "max_cell_count": int(d.max_cell_count)}
 
     def geometry(self) -> dict:

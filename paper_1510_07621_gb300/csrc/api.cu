@@ -88,6 +88,54 @@ double quad(const p3m_cosmology &cs, double a1, double a2, int power)
     return 0.5 * (a2 - a1) * s;
 }
 
+// ---------------------------------------------------------------- split factor fit
+// g(x) = erfc(x/2) + x/sqrt(pi) exp(-x^2/4) = 1 + x^3 Q(x^2).  Q is smooth in u = x^2; it is
+// interpolated at 40 Chebyshev-Gauss nodes of u in [0, u_c], u_c = (r_c/r_s)^2, truncated to
+// degree 10 (a near-minimax polynomial), and rewritten in monomial form in tau = 2u/u_c - 1
+// for Horner evaluation in FP32.  The kernel evaluates g = 1 + r^3 Q'(tau) directly from
+// r^2, so the coefficients are scaled by r_s^-3 and tau = r^2 (2 / (u_c r_s^2)) - 1.
+
+double split_q(double u)
+{
+    const double x = sqrt(u), inv_sqrt_pi = 0.56418958354775628695;
+    if (u < 1e-6) return -inv_sqrt_pi / 6.0 * (1.0 - 0.15 * u);  // series: -(1/(6 sqrt pi))(1 - 3u/20)
+    const double gval = erfc(0.5 * x) + x * inv_sqrt_pi * exp(-0.25 * u);
+    return (gval - 1.0) / (u * x);
+}
+
+void fit_split_poly(double cutoff_in_rs, double r_s, float out[12])
+{
+    const int deg = 10, nodes = 40;
+    const double uc = cutoff_in_rs * cutoff_in_rs;
+    double cheb[deg + 1] = {0};
+    for (int j = 0; j < nodes; ++j) {
+        const double th = M_PI * (j + 0.5) / nodes, t = cos(th);
+        const double q = split_q(0.5 * (t + 1.0) * uc);
+        for (int k = 0; k <= deg; ++k) cheb[k] += q * cos(k * th);
+    }
+    for (int k = 0; k <= deg; ++k) cheb[k] *= (k == 0 ? 1.0 : 2.0) / nodes;
+    // Chebyshev series -> monomials: T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1}
+    double tk_prev[deg + 1] = {0}, tk[deg + 1] = {0}, mono[deg + 1] = {0};
+    tk_prev[0] = 1.0;
+    tk[1] = 1.0;
+    mono[0] += cheb[0];
+    for (int i = 0; i <= deg; ++i) mono[i] += cheb[1] * tk[i];
+    for (int k = 2; k <= deg; ++k) {
+        double next[deg + 1] = {0};
+        for (int i = 0; i <= deg; ++i) {
+            next[i] = -tk_prev[i] + (i > 0 ? 2.0 * tk[i - 1] : 0.0);
+        }
+        for (int i = 0; i <= deg; ++i) {
+            mono[i] += cheb[k] * next[i];
+            tk_prev[i] = tk[i];
+            tk[i] = next[i];
+        }
+    }
+    const double inv_rs3 = 1.0 / (r_s * r_s * r_s);
+    for (int i = 0; i <= deg; ++i) out[i] = (float)(mono[i] * inv_rs3);
+    out[11] = (float)(2.0 / (uc * r_s * r_s));
+}
+
 // ---------------------------------------------------------------- phase timing
 
 struct Phase {
@@ -136,7 +184,8 @@ void release(p3m_ctx *c)
                     c->keys_alt,  c->vals,     c->vals_alt,     c->digit_counts, c->scan_aux,
                     c->cell_start, c->work,    c->work_off,     c->counters, c->pair_count,
                     c->red,       c->rho,      c->rho_k,        c->frc_k,    c->frc,
-                    c->tab_k,     c->tab_kg,   c->tab_g};
+                    c->tab_k,     c->tab_kg,   c->tab_g,        c->work_key, c->work_key_alt,
+                    c->work_order, c->work_order_alt, c->block_box};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -280,7 +329,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
     if (cosmo) cs = *cosmo;
 
     if (!finite_pos(box)) return fail(c, P3M_EINVAL, "p3m_init: box must be finite and > 0");
-    if (n < 1 || n >= (int64_t)1 << 32) return fail(c, P3M_EINVAL, "p3m_init: n must be in [1, 2^32)");
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(c, P3M_EINVAL, "p3m_init: n must be in [1, 2^31)");
     if (mesh < 8 || mesh > 2048 || (mesh & 1))
         return fail(c, P3M_EINVAL, "p3m_init: mesh must be even and in [8, 2048]");
     if (!finite_pos(r_s_cells)) return fail(c, P3M_EINVAL, "p3m_init: r_s_cells must be > 0");
@@ -351,8 +400,9 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         }
         const size_t N = (size_t)n, M = (size_t)mesh, nk = M * M * (M / 2 + 1), M3 = M * M * M;
         const size_t real = c->precision == P3M_PREC_MIXED ? 4 : 8;
-        c->n_tiles = (int)((N + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
         c->max_work = N / P3M_PAIR_TI + (size_t)g.n_cells + 1;
+        const size_t nsort = N > c->max_work ? N : c->max_work;  // longest array the sorts see
+        c->n_tiles = (int)((nsort + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
         const size_t scan_n = (size_t)256 * c->n_tiles > (size_t)g.n_cells + 1 ? (size_t)256 * c->n_tiles
                                                                                : (size_t)g.n_cells + 1;
         struct {
@@ -364,12 +414,15 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->pos_alt, 24 * N},   {(void **)&c->mom_alt, 24 * N},
             {(void **)&c->pid, 4 * N},        {(void **)&c->pid_alt, 4 * N},
             {(void **)&c->rel, 4 * real * N}, {(void **)&c->keys, 4 * N},
+            {(void **)&c->block_box, 32 * ((N + 31) / 32)},
             {(void **)&c->keys_alt, 4 * N},   {(void **)&c->vals, 4 * N},
             {(void **)&c->vals_alt, 4 * N},   {(void **)&c->digit_counts, 4 * 256 * (size_t)c->n_tiles},
             {(void **)&c->scan_aux, 4 * (scan_n / P3M_SORT_TILE + 4)},
             {(void **)&c->cell_start, 4 * ((size_t)g.n_cells + 1)},
             {(void **)&c->work, 8 * c->max_work}, {(void **)&c->work_off, 4 * ((size_t)g.n_cells + 1)},
-            {(void **)&c->counters, 16},      {(void **)&c->pair_count, 16},
+            {(void **)&c->work_key, 4 * c->max_work}, {(void **)&c->work_key_alt, 4 * c->max_work},
+            {(void **)&c->work_order, 4 * c->max_work}, {(void **)&c->work_order_alt, 4 * c->max_work},
+            {(void **)&c->counters, 16},      {(void **)&c->pair_count, 64},
             {(void **)&c->red, 8 * (1024 * 4 + 8)},
             {(void **)&c->rho, real * M3},    {(void **)&c->rho_k, 2 * real * nk},
             {(void **)&c->frc_k, 6 * real * nk}, {(void **)&c->frc, 3 * real * M3},
@@ -386,7 +439,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         }
         if (rc != P3M_OK) break;
         cudaMemsetAsync(c->counters, 0, 16, c->stream);
-        cudaMemsetAsync(c->pair_count, 0, 16, c->stream);
+        cudaMemsetAsync(c->pair_count, 0, 64, c->stream);
 
         // per-axis tables (FP64 on the host, stored in the mesh precision)
         const double h = box / mesh, rs2 = c->short_range ? g.r_s * g.r_s : 0.0;
@@ -405,6 +458,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             tg[i] = t;
         }
         c->green_const = -4.0 * M_PI * (g.gm / (h * h * h)) / ((double)M3);
+        fit_split_poly(cutoff_in_rs, g.r_s, c->gpoly);
         if (c->precision == P3M_PREC_MIXED) {
             std::vector<float> f(M);
             const std::vector<double> *src[3] = {&tk, &tkg, &tg};
@@ -599,12 +653,15 @@ extern "C" int p3m_diagnostics(p3m_ctx *c, p3m_diag *out)
     out->momentum[1] = r[1];
     out->momentum[2] = r[2];
     out->kinetic = r[3] / (2.0 * c->mass * c->a * c->a);
-    unsigned long long pc[2] = {0, 0};
+    unsigned long long pc[5] = {0, 0, 0, 0, 0};
     uint32_t mc = 0;
     CK(cudaMemcpy(pc, c->pair_count, sizeof(pc), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&mc, c->counters + 2, sizeof(mc), cudaMemcpyDeviceToHost));
     out->pairs = pc[0];
     out->pairs_total = pc[1];
+    out->pair_warp_j[0] = pc[2];
+    out->pair_warp_j[1] = pc[3];
+    out->pair_warp_j[2] = pc[4];
     out->launches = c->launches;
     out->max_cell_count = (int32_t)mc;
     return check_flags(c);

@@ -42,6 +42,7 @@ struct p3m_ctx {
     double *pos_alt, *mom_alt;  // permute targets / staging
     uint32_t *pid_alt;
     void *rel;  // float4 (mixed) or double4 (fp64): position relative to its cell origin
+    float4 *block_box;  // per 32-slot block of the sorted order: lo, hi (FP32, absolute)
 
     // sort
     uint32_t *keys, *keys_alt, *vals, *vals_alt;
@@ -52,6 +53,8 @@ struct p3m_ctx {
     uint32_t *cell_start;  // n_cells + 1
     uint32_t *work;        // pair work items (cell, first slot)
     uint32_t *work_off;    // n_cells + 1
+    uint32_t *work_key, *work_key_alt;      // cost keys of the work items (max_work)
+    uint32_t *work_order, *work_order_alt;  // work items, most expensive first (max_work)
     size_t max_work;
     uint32_t *counters;  // [0] work cursor [1] error flags [2] max cell count [3] spare
     unsigned long long *pair_count;  // [0] last evaluation [1] cumulative
@@ -62,6 +65,8 @@ struct p3m_ctx {
     void *rho, *rho_k, *frc_k, *frc;
     void *tab_k, *tab_kg, *tab_g;  // per-axis |k|, gradient k, Green factor (length M)
     double green_const;
+    float gpoly[12];  // FP32 split factor: g = 1 + x u Q(tau), Q = sum gpoly[k] tau^k (k <= 10),
+                      // tau = u gpoly[11] - 1, u = (r/r_s)^2
     cufftHandle plan_r2c, plan_c2r;
     bool plans_made;
 
@@ -92,8 +97,8 @@ enum {
 };
 
 #define P3M_SORT_TILE 4096   // keys per radix-sort tile (256 threads x 16)
-#define P3M_PAIR_TI 128      // i-particles per pair work item (one per thread)
-#define P3M_PAIR_TJ 256      // j-particles per shared-memory tile
+#define P3M_PAIR_TI 32       // i-particles per pair work item (one per lane of a warp)
+#define P3M_PAIR_TJ 128      // j-particles per shared-memory tile (4 blocks of 32)
 #define P3M_FLAG_TIMEOUT 1u  // counters[1] bit: a bounded wait gave up
 #define P3M_FLAG_NONFINITE 2u
 

@@ -7,22 +7,29 @@
 // over the particles of the 27 chaining cells around particle i's cell (n_c >= 3 cells of
 // side >= r_c, so each neighbour cell appears once and with the minimum image).
 //
-// Work item = up to 128 particles of one cell (one per thread).  The j particles of the 27
-// neighbour cells stream through shared memory in tiles of 256, copied by the bulk-copy (TMA)
-// engine into two alternating buffers (the next tile is in flight while the current one is
-// used), completion tracked by one mbarrier per buffer.  Coordinates are relative to each
-// particle's own cell origin (FP32 in the mixed mode), shifted per neighbour cell by the
-// FP64 offset between the two cell origins, so no FP32 absolute coordinate ever appears.
-// Per-tile FP32 partial sums are added into FP64 accumulators per particle.
-// CTAs are persistent and take work items from an atomic cursor.
+// Layout of the work: a CTA is one warp and a work item is up to 32 particles of one cell (one
+// per lane).  The warp streams the j particles of the 27 neighbour cells through shared memory
+// in tiles of up to four 32-slot blocks of the sorted order, copied by the bulk-copy (TMA)
+// engine into two alternating buffers (the next tile in flight while the current one is used;
+// one mbarrier per buffer; every wait bounded).  The warp skips a block when no lane's particle
+// is within r_c of the block's bounding box, evaluates it without per-pair tests when the box
+// lies within r_c of every lane's particle, and otherwise tests each pair, skipping j's that
+// no lane accepts.  CTAs are persistent and take work items, most expensive first, from an
+// atomic cursor.  No CTA-wide barrier: warps never wait for each other.
+//
+// Precision: FP32 mode uses coordinates relative to each particle's own cell origin (FP32),
+// shifted per neighbour cell by the FP64 offset between the two cell origins, per-tile FP32
+// partial sums added into FP64 accumulators, and g from a fitted polynomial (below).  FP64 mode
+// keeps absolute coordinates (d = (x_j - x_i) + image, like a plain minimum-image difference)
+// and evaluates g with erfc/exp.
 #include <cuda_runtime.h>
 
 #include "p3m_internal.cuh"
 
 namespace {
 
-constexpr int kTI = P3M_PAIR_TI;
-constexpr int kTJ = P3M_PAIR_TJ;
+constexpr int kTJ = P3M_PAIR_TJ;  // 128
+constexpr int kBlocksPerTile = kTJ / 32;
 
 template <typename T>
 struct Vec4;
@@ -93,16 +100,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
-// Pair kernel g(x) * (r^2 + eps^2)^-3/2 for one pair with r2 = |d|^2 (0 < r2 < r_c^2).
-__device__ __forceinline__ float pair_factor(float r2, float eps2, float inv_rs)
+__device__ __forceinline__ float rsqrt_approx(float x)
 {
-    const float s = rsqrtf(r2 + eps2);
-    const float x = r2 * rsqrtf(r2) * inv_rs;
-    const float g = erfcf(0.5f * x) + x * 0.564189583547756287f * expf(-0.25f * x * x);
-    return g * s * s * s;
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-__device__ __forceinline__ double pair_factor(double r2, double eps2, double inv_rs)
+// Coefficients of the FP32 split factor, fitted on the host for the context's cutoff:
+// g = 1 + r^3 sum_k c[k] tau^k (k = 0..10), tau = r^2 c[11] - 1.
+struct GPoly {
+    float c[12];
+};
+
+// g(r/r_s) (r^2 + eps^2)^-3/2 for one pair, FP32.  Only meaningful for 0 < r2 < r_c^2; the
+// caller selects 0 for every other pair (r2 = 0 gives inf/NaN here, which the select drops).
+__device__ __forceinline__ float pair_factor32(float r2, float eps2, const GPoly &gp)
+{
+    const float t = rsqrt_approx(r2);
+    const float s = rsqrt_approx(r2 + eps2);
+    const float r = r2 * t;
+    const float r3 = r2 * r;
+    const float tau = fmaf(r2, gp.c[11], -1.0f);
+    float p = gp.c[10];
+#pragma unroll
+    for (int k = 9; k >= 0; --k) p = fmaf(p, tau, gp.c[k]);
+    const float gval = fmaf(r3, p, 1.0f);
+    return gval * (s * s * s);
+}
+
+// The same in FP64, g from erfc and exp.
+__device__ __forceinline__ double pair_factor64(double r2, double eps2, double inv_rs)
 {
     const double s = 1.0 / sqrt(r2 + eps2);
     const double x = sqrt(r2) * inv_rs;
@@ -110,163 +138,224 @@ __device__ __forceinline__ double pair_factor(double r2, double eps2, double inv
     return g * s * s * s;
 }
 
+template <typename T>
+__device__ __forceinline__ T pair_factor(T r2, T eps2, const GPoly &gp, double inv_rs);
+template <>
+__device__ __forceinline__ float pair_factor<float>(float r2, float eps2, const GPoly &gp, double)
+{
+    return pair_factor32(r2, eps2, gp);
+}
+template <>
+__device__ __forceinline__ double pair_factor<double>(double r2, double eps2, const GPoly &,
+                                                      double inv_rs)
+{
+    return pair_factor64(r2, eps2, inv_rs);
+}
+
 struct Neighbour {
     uint32_t start, end;
-    double sx, sy, sz;  // origin(neighbour, unwrapped image) - origin(own cell)
+    double sx, sy, sz;     // FP32 mode: origin(neighbour) - origin(own cell), image included;
+                           // FP64 mode: the periodic image only
+    double imx, imy, imz;  // periodic image (both modes)
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kTI)
-    k_pairs(const typename Vec4<T>::type *__restrict__ rel, const uint32_t *__restrict__ cell_start,
-            const uint32_t *__restrict__ work, const uint32_t *__restrict__ n_work_ptr, P3MGeom g,
+__global__ void __launch_bounds__(32)
+    k_pairs(const typename Vec4<T>::type *__restrict__ rel, const double *__restrict__ pos,
+            const float4 *__restrict__ block_box, const uint32_t *__restrict__ cell_start,
+            const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
+            const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPoly gp, float rcull2, float rin2,
             const double *__restrict__ acc_in, double *__restrict__ acc_out,
             double *__restrict__ mom, double kfac, uint32_t *__restrict__ counters,
             unsigned long long *__restrict__ pair_count)
 {
     using V4 = typename Vec4<T>::type;
-    // FP64 mode keeps absolute coordinates (d = (x_j - x_i) + image, the same operations as a
-    // plain minimum-image difference); FP32 mode uses cell-relative coordinates.
     constexpr bool kAbsolute = sizeof(T) == 8;
     __shared__ __align__(128) V4 sj[2][kTJ];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ Neighbour nbr[27];
-    __shared__ uint32_t s_item;
 
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x;
     const int64_t n = g.n;
     const uint32_t n_work = *n_work_ptr;
     const T rc2 = (T)(g.r_c * g.r_c);
     const T eps2 = (T)(g.eps * g.eps);
-    const T inv_rs = (T)(1.0 / g.r_s);
+    const double inv_rs = 1.0 / g.r_s;
     const int nc = g.n_c;
 
-    if (tid == 0) {
+    if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
     }
-    __syncthreads();
-    uint32_t parity[2] = {0u, 0u};
-    unsigned long long my_pairs = 0;
+    __syncwarp();
+    uint32_t parity = 0u;  // bit b: parity of the next phase of bar[b]
+    unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0;
+    bool timed_out = false;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&counters[0], 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= n_work) break;
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(&counters[0], 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= n_work) break;
+        const uint32_t item = order[slot];
         const uint32_t cell = work[2 * (size_t)item];
         const uint32_t first = work[2 * (size_t)item + 1];
         const uint32_t cend = cell_start[cell + 1];
         const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
-        if (tid < 27) {
-            const int ox = tid % 3 - 1, oy = (tid / 3) % 3 - 1, oz = tid / 9 - 1;
-            int ux = cx + ox, uy = cy + oy, uz = cz + oz;  // unwrapped neighbour index
+        if (lane < 27) {
+            const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+            const int ux = cx + ox, uy = cy + oy, uz = cz + oz;  // unwrapped neighbour index
             const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
             const uint32_t nb = ((uint32_t)wz * nc + wy) * nc + wx;
             Neighbour q;
             q.start = cell_start[nb];
             q.end = cell_start[nb + 1];
             const double L = g.box, cs = g.cs;
-            const double ix = ux < 0 ? -L : (ux >= nc ? L : 0.0);
-            const double iy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
-            const double iz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
-            if (kAbsolute) {  // periodic image only
-                q.sx = ix;
-                q.sy = iy;
-                q.sz = iz;
-            } else {  // offset between the two cell origins (image included)
-                q.sx = ((double)wx * cs + ix) - (double)cx * cs;
-                q.sy = ((double)wy * cs + iy) - (double)cy * cs;
-                q.sz = ((double)wz * cs + iz) - (double)cz * cs;
+            q.imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+            q.imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+            q.imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            if (kAbsolute) {
+                q.sx = q.imx;
+                q.sy = q.imy;
+                q.sz = q.imz;
+            } else {
+                q.sx = ((double)wx * cs + q.imx) - (double)cx * cs;
+                q.sy = ((double)wy * cs + q.imy) - (double)cy * cs;
+                q.sz = ((double)wz * cs + q.imz) - (double)cz * cs;
             }
-            nbr[tid] = q;
+            nbr[lane] = q;
         }
-        __syncthreads();
+        __syncwarp();
 
-        const uint32_t i = first + tid;
+        const uint32_t i = first + lane;
         const bool valid = i < cend;
-        V4 xi = valid ? rel[i] : V4{};
+        const uint32_t ii = valid ? i : first;
+        const V4 xi = rel[ii];
+        const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];  // absolute, FP64
         double ax = 0.0, ay = 0.0, az = 0.0;
 
-        // tile sequence: neighbour nb, tile start js; (27, *) = done
-        int nb_c = 0;
-        uint32_t js_c = nbr[0].start;
-        auto advance = [&](int &nb, uint32_t &js) {
-            // move (nb, js) to the next non-empty tile position at or after it
-            while (nb < 27 && js >= nbr[nb].end) {
+        // Tile sequence over (neighbour nb, first block b); a tile is the blocks [b, b + 4)
+        // clipped to the neighbour's range of slots; nb == 27 ends the sequence.
+        auto next_tile = [&](int &nb, uint32_t &b) {
+            while (nb < 27 && b * 32u >= nbr[nb].end) {
                 ++nb;
-                if (nb < 27) js = nbr[nb].start;
+                if (nb < 27) b = nbr[nb].start >> 5;
             }
         };
-        advance(nb_c, js_c);
+        auto issue = [&](int nb, uint32_t b, int to) {
+            const uint32_t bend = min(b + kBlocksPerTile, (nbr[nb].end + 31) >> 5);
+            const uint32_t j0 = b * 32;
+            const uint32_t j1 = min((uint32_t)n, bend * 32);
+            const uint32_t bytes = (j1 - j0) * (uint32_t)sizeof(V4);
+            mbar_expect_tx(&bar[to], bytes);
+            bulk_load(&sj[to][0], rel + j0, bytes, &bar[to]);
+        };
+
+        int nb_c = 0;
+        uint32_t b_c = nbr[0].start >> 5;
+        next_tile(nb_c, b_c);
         int buf = 0;
-        if (nb_c < 27 && tid == 0) {
-            const uint32_t len = min((uint32_t)kTJ, nbr[nb_c].end - js_c);
-            mbar_expect_tx(&bar[0], len * (uint32_t)sizeof(V4));
-            bulk_load(&sj[0][0], rel + js_c, len * (uint32_t)sizeof(V4), &bar[0]);
-        }
-        bool timed_out = false;
+        if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
         while (nb_c < 27) {
-            const uint32_t len = min((uint32_t)kTJ, nbr[nb_c].end - js_c);
+            const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
+            const uint32_t bend = min(b_c + kBlocksPerTile, (nend + 31) >> 5);
             int nb_n = nb_c;
-            uint32_t js_n = js_c + len;
-            advance(nb_n, js_n);
-            if (nb_n < 27 && tid == 0) {
-                const uint32_t ln = min((uint32_t)kTJ, nbr[nb_n].end - js_n);
-                mbar_expect_tx(&bar[buf ^ 1], ln * (uint32_t)sizeof(V4));
-                bulk_load(&sj[buf ^ 1][0], rel + js_n, ln * (uint32_t)sizeof(V4), &bar[buf ^ 1]);
-            }
-            const bool ok = mbar_wait_bounded(&bar[buf], parity[buf]);
-            parity[buf] ^= 1u;
-            if (__syncthreads_or(!ok)) {
+            uint32_t b_n = bend;
+            next_tile(nb_n, b_n);
+            __syncwarp();  // every lane is done with sj[buf ^ 1] before it is refilled
+            if (nb_n < 27 && lane == 0) issue(nb_n, b_n, buf ^ 1);
+            const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+            parity ^= 1u << buf;
+            if (__any_sync(0xffffffffu, !ok)) {
                 timed_out = true;
-                if (nb_n < 27) {  // drain the copy in flight into the other buffer
-                    mbar_wait_bounded(&bar[buf ^ 1], parity[buf ^ 1]);
-                }
+                if (nb_n < 27) mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
                 break;
             }
+            const Neighbour &q = nbr[nb_c];
             // FP32: xs = x_i - shift, d = x_j - xs;  FP64: d = (x_j - x_i) + image
-            const T xs = kAbsolute ? (T)xi.x : (T)((double)xi.x - nbr[nb_c].sx);
-            const T ys = kAbsolute ? (T)xi.y : (T)((double)xi.y - nbr[nb_c].sy);
-            const T zs = kAbsolute ? (T)xi.z : (T)((double)xi.z - nbr[nb_c].sz);
-            const T ix = kAbsolute ? (T)nbr[nb_c].sx : T(0);
-            const T iy = kAbsolute ? (T)nbr[nb_c].sy : T(0);
-            const T iz = kAbsolute ? (T)nbr[nb_c].sz : T(0);
-            T px = 0, py = 0, pz = 0;
-            uint32_t cnt = 0;
+            const T xs = kAbsolute ? (T)xi.x : (T)((double)xi.x - q.sx);
+            const T ys = kAbsolute ? (T)xi.y : (T)((double)xi.y - q.sy);
+            const T zs = kAbsolute ? (T)xi.z : (T)((double)xi.z - q.sz);
+            const T ix = kAbsolute ? (T)q.sx : T(0);
+            const T iy = kAbsolute ? (T)q.sy : T(0);
+            const T iz = kAbsolute ? (T)q.sz : T(0);
+            // particle i in the frame of the block boxes (absolute, image removed)
+            const float cxs = (float)(xa - q.imx), cys = (float)(ya - q.imy), czs = (float)(za - q.imz);
             const V4 *tile = sj[buf];
-            for (uint32_t j = 0; j < len; ++j) {
-                const V4 q = tile[j];
-                T dx = q.x - xs, dy = q.y - ys, dz = q.z - zs;
-                if (kAbsolute) {
-                    dx += ix;
-                    dy += iy;
-                    dz += iz;
+            T px = 0, py = 0, pz = 0;
+            uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0;
+            for (uint32_t b = b_c; b < bend; ++b) {
+                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
+                const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
+                const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
+                const bool near = valid && ex * ex + ey * ey + ez * ez < rcull2;
+                if (!__any_sync(0xffffffffu, near)) continue;
+                // the block's slots that belong to the neighbour cell, as tile offsets
+                const uint32_t j0 = max(b * 32, nstart) - b_c * 32;
+                const uint32_t j1 = min(b * 32 + 32, nend) - b_c * 32;
+                const float fx = fmaxf(cxs - lo.x, hi.x - cxs);
+                const float fy = fmaxf(cys - lo.y, hi.y - cys);
+                const float fz = fmaxf(czs - lo.z, hi.z - czs);
+                if (__all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2)) {
+                    // the block lies within r_c of every particle of the warp
+                    n_fast += j1 - j0;
+#pragma unroll 2
+                    for (uint32_t j = j0; j < j1; ++j) {
+                        const V4 qj = tile[j];
+                        T dx = qj.x - xs, dy = qj.y - ys, dz = qj.z - zs;
+                        if (kAbsolute) {
+                            dx += ix;
+                            dy += iy;
+                            dz += iz;
+                        }
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        const bool in = valid && r2 > T(0);
+                        T f = pair_factor<T>(r2, eps2, gp, inv_rs);
+                        f = in ? f : T(0);
+                        px += f * dx;
+                        py += f * dy;
+                        pz += f * dz;
+                        cnt += in ? 1u : 0u;
+                    }
+                    continue;
                 }
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < rc2 && r2 > T(0)) {
-                    const T f = pair_factor(r2, eps2, inv_rs);
+                n_tested += j1 - j0;
+                for (uint32_t j = j0; j < j1; ++j) {
+                    const V4 qj = tile[j];
+                    T dx = qj.x - xs, dy = qj.y - ys, dz = qj.z - zs;
+                    if (kAbsolute) {
+                        dx += ix;
+                        dy += iy;
+                        dz += iz;
+                    }
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    const bool in = valid && r2 < rc2 && r2 > T(0);
+                    if (!__any_sync(0xffffffffu, in)) continue;
+                    ++n_eval;
+                    T f = pair_factor<T>(r2, eps2, gp, inv_rs);
+                    f = in ? f : T(0);
                     px += f * dx;
                     py += f * dy;
                     pz += f * dz;
-                    ++cnt;
+                    cnt += in ? 1u : 0u;
                 }
             }
             ax += (double)px;
             ay += (double)py;
             az += (double)pz;
-            if (valid) my_pairs += cnt;
-            __syncthreads();  // every thread is done with sj[buf] before it is refilled
+            my_pairs += cnt;
+            st_fast += n_fast;
+            st_tested += n_tested;
+            st_eval += n_eval;
             buf ^= 1;
             nb_c = nb_n;
-            js_c = js_n;
+            b_c = b_n;
         }
-        if (timed_out) {
-            if (tid == 0) atomicOr(&counters[1], P3M_FLAG_TIMEOUT);
-            break;
-        }
+        if (timed_out) break;
         if (valid) {
-            double a3[3] = {g.gm * ax, g.gm * ay, g.gm * az};
+            const double a3[3] = {g.gm * ax, g.gm * ay, g.gm * az};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double tot = (acc_in ? acc_in[d * n + i] : 0.0) + a3[d];
@@ -274,13 +363,20 @@ __global__ void __launch_bounds__(kTI)
                 if (kfac != 0.0) mom[d * n + i] = __dadd_rn(mom[d * n + i], __dmul_rn(kfac, tot));
             }
         }
+        __syncwarp();  // nbr is rewritten by the next item
     }
+    if (timed_out && lane == 0) atomicOr(&counters[1], P3M_FLAG_TIMEOUT);
     // pair count: warp sum, one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
-    if ((tid & 31) == 0 && my_pairs) {
-        atomicAdd(pair_count, my_pairs);
-        atomicAdd(pair_count + 1, my_pairs);
+    if (lane == 0) {
+        if (my_pairs) {
+            atomicAdd(pair_count, my_pairs);
+            atomicAdd(pair_count + 1, my_pairs);
+        }
+        if (st_fast) atomicAdd(pair_count + 2, st_fast);
+        if (st_tested) atomicAdd(pair_count + 3, st_tested);
+        if (st_eval) atomicAdd(pair_count + 4, st_eval);
     }
 }
 
@@ -288,16 +384,24 @@ template <typename T>
 cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac)
 {
     cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
-    cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);  // last evaluation
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<T>, kTI, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<T>, 32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int grid = c->num_sms * per_sm;
+    GPoly gp;
+    for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
+    // culling radii: r_c widened (narrowed) by more than the FP32 rounding of absolute
+    // coordinates up to the box size
+    const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
+    const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
     c->launches += 1;
-    k_pairs<T><<<grid, kTI, 0, c->stream>>>((const typename Vec4<T>::type *)c->rel, c->cell_start,
-                                            c->work, c->work_off + c->g.n_cells, c->g, acc_in,
-                                            acc_out, c->mom, kfac, c->counters, c->pair_count);
+    k_pairs<T><<<grid, 32, 0, c->stream>>>(
+        (const typename Vec4<T>::type *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
+        c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
+        rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, c->counters,
+        c->pair_count);
     return cudaGetLastError();
 }
 

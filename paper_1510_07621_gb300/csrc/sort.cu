@@ -261,23 +261,48 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
                           P3MGeom g, const double *__restrict__ pos,
                           const double *__restrict__ mom, const uint32_t *__restrict__ pid,
                           double *__restrict__ pos_out, double *__restrict__ mom_out,
-                          uint32_t *__restrict__ pid_out, R4 *__restrict__ rel)
+                          uint32_t *__restrict__ pid_out, R4 *__restrict__ rel,
+                          float4 *__restrict__ block_box)
 {
+    // one warp per 32-slot block of the sorted order; the warp also writes the block's
+    // bounding box (FP32, absolute coordinates, rounded outwards by the callers' margins)
     const int64_t n = g.n;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t j = perm[k];
+    const int64_t nblocks = (n + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
+         blk += nwarps) {
+        const int64_t k = blk * 32 + lane;
+        const bool active = k < n;
+        const uint32_t j = perm[active ? k : blk * 32];
         const double x = pos[j], y = pos[n + j], z = pos[2 * n + j];
-        pos_out[k] = x;
-        pos_out[n + k] = y;
-        pos_out[2 * n + k] = z;
-        mom_out[k] = mom[j];
-        mom_out[n + k] = mom[n + j];
-        mom_out[2 * n + k] = mom[2 * n + j];
-        pid_out[k] = pid[j];
-        const uint32_t cell = keys[k] >> (3 * g.sub_bits);
-        const uint32_t cx = cell % g.n_c, cy = (cell / g.n_c) % g.n_c, cz = cell / (g.n_c * g.n_c);
-        rel[k] = rel_coords<R4>(x, y, z, cx, cy, cz, g.cs);
+        if (active) {
+            pos_out[k] = x;
+            pos_out[n + k] = y;
+            pos_out[2 * n + k] = z;
+            mom_out[k] = mom[j];
+            mom_out[n + k] = mom[n + j];
+            mom_out[2 * n + k] = mom[2 * n + j];
+            pid_out[k] = pid[j];
+            const uint32_t cell = keys[k] >> (3 * g.sub_bits);
+            const uint32_t cx = cell % g.n_c, cy = (cell / g.n_c) % g.n_c,
+                           cz = cell / (g.n_c * g.n_c);
+            rel[k] = rel_coords<R4>(x, y, z, cx, cy, cz, g.cs);
+        }
+        float lx = (float)x, ly = (float)y, lz = (float)z, hx = lx, hy = ly, hz = lz;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+        if (lane == 0) {
+            block_box[2 * blk] = make_float4(lx, ly, lz, 0.0f);
+            block_box[2 * blk + 1] = make_float4(hx, hy, hz, 0.0f);
+        }
     }
 }
 
@@ -305,17 +330,35 @@ __global__ void k_work_count(const uint32_t *__restrict__ cell_start, int n_cell
     }
 }
 
-// Work item = (cell << 0, first slot) packed as two uint32: work[2w] = cell, work[2w+1] = slot.
+// Work item w = (cell, first slot): work[2w] = cell, work[2w+1] = slot.  Its cost estimate is
+// (particles in the item) x (particles in the 27 neighbour cells); the sort key is the top 16
+// bits of that cost as an FP32 number, inverted, so that an ascending sort puts the most
+// expensive items first.  Unused entries keep the key 0xFFFFFFFF and sort last.
 __global__ void k_work_fill(const uint32_t *__restrict__ cell_start,
-                            const uint32_t *__restrict__ work_off, int n_cells,
-                            uint32_t *__restrict__ work)
+                            const uint32_t *__restrict__ work_off, int n_c,
+                            uint32_t *__restrict__ work, uint32_t *__restrict__ work_key,
+                            uint32_t *__restrict__ work_val)
 {
+    const int n_cells = n_c * n_c * n_c;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
         const uint32_t s = cell_start[c], e = cell_start[c + 1];
+        if (s == e) continue;
+        const int cx = c % n_c, cy = (c / n_c) % n_c, cz = c / (n_c * n_c);
+        float nb = 0.0f;
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int q = (((cz + oz + n_c) % n_c) * n_c + (cy + oy + n_c) % n_c) * n_c +
+                                  (cx + ox + n_c) % n_c;
+                    nb += (float)(cell_start[q + 1] - cell_start[q]);
+                }
         uint32_t w = work_off[c];
         for (uint32_t i = s; i < e; i += P3M_PAIR_TI, ++w) {
             work[2 * (size_t)w] = (uint32_t)c;
             work[2 * (size_t)w + 1] = i;
+            const float cost = (float)min((uint32_t)P3M_PAIR_TI, e - i) * nb;
+            work_key[w] = 0xFFFFu - (__float_as_uint(cost) >> 16);
+            work_val[w] = w;
         }
     }
 }
@@ -349,42 +392,54 @@ cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_radix_sort(p3m_ctx *c)
+// Stable LSD sort of n (key, value) pairs on the low key_bits bits.  k[0]/v[0] hold the input
+// (v[0] NULL: values are the input positions); on return k[0]/v[0] hold the sorted pairs (the
+// two buffers of each array are swapped as needed).  counts needs 256 * ceil(n/4096) entries.
+cudaError_t radix_sort_pairs(uint32_t **k, uint32_t **v, bool identity_vals, int64_t n,
+                             int key_bits, uint32_t *counts, uint32_t *aux, cudaStream_t s,
+                             unsigned long long *launches)
 {
-    const int64_t n = c->g.n;
-    const int passes = (c->key_bits + kRadixBits - 1) / kRadixBits;
-    const size_t ncount = (size_t)kRadix * c->n_tiles;
-    uint32_t *kin = c->keys, *kout = c->keys_alt;
-    uint32_t *vin = nullptr, *vout = c->vals;
+    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    const int n_tiles = (int)((n + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
+    const size_t ncount = (size_t)kRadix * n_tiles;
+    uint32_t *kin = k[0], *kout = k[1];
+    uint32_t *vin = identity_vals ? nullptr : v[0], *vout = identity_vals ? v[0] : v[1];
     for (int p = 0; p < passes; ++p) {
         const int shift = p * kRadixBits;
-        c->launches += 5;  // upsweep, 3 scan kernels, downsweep
-        k_radix_upsweep<<<c->n_tiles, kThreads, 0, c->stream>>>(kin, n, shift, c->digit_counts,
-                                                                c->n_tiles);
-        cudaError_t e = launch_scan_u32(c->digit_counts, c->digit_counts, ncount, c->scan_aux,
-                                        c->stream);
+        *launches += 5;  // upsweep, 3 scan kernels, downsweep
+        k_radix_upsweep<<<n_tiles, kThreads, 0, s>>>(kin, n, shift, counts, n_tiles);
+        cudaError_t e = launch_scan_u32(counts, counts, ncount, aux, s);
         if (e != cudaSuccess) return e;
-        k_radix_downsweep<<<c->n_tiles, kThreads, 0, c->stream>>>(
-            kin, vin, n, shift, c->digit_counts, c->n_tiles, kout, vout);
-        // next pass reads what this one wrote
-        uint32_t *t = kin;
+        k_radix_downsweep<<<n_tiles, kThreads, 0, s>>>(kin, vin, n, shift, counts, n_tiles, kout,
+                                                       vout);
+        uint32_t *t = kin;  // the next pass reads what this one wrote
         kin = kout;
         kout = t;
+        uint32_t *vt = vin;
         vin = vout;
-        vout = (vout == c->vals) ? c->vals_alt : c->vals;
+        vout = vt ? vt : v[1];
     }
-    // make c->keys / c->vals the sorted result
-    if (kin != c->keys) {
-        uint32_t *t = c->keys;
-        c->keys = kin;
-        c->keys_alt = t;
+    if (kin != k[0]) {
+        k[1] = k[0];
+        k[0] = kin;
     }
-    if (vin != c->vals) {
-        uint32_t *t = c->vals;
-        c->vals = vin;
-        c->vals_alt = t;
+    if (vin != v[0]) {
+        v[1] = v[0];
+        v[0] = vin;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_radix_sort(p3m_ctx *c)
+{
+    uint32_t *k[2] = {c->keys, c->keys_alt}, *v[2] = {c->vals, c->vals_alt};
+    cudaError_t e = radix_sort_pairs(k, v, true, c->g.n, c->key_bits, c->digit_counts, c->scan_aux,
+                                     c->stream, &c->launches);
+    c->keys = k[0];
+    c->keys_alt = k[1];
+    c->vals = v[0];
+    c->vals_alt = v[1];
+    return e;
 }
 
 cudaError_t launch_permute_and_cells(p3m_ctx *c)
@@ -395,11 +450,11 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     if (c->precision == P3M_PREC_MIXED)
         k_permute<float4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                      c->pid, c->pos_alt, c->mom_alt, c->pid_alt,
-                                                     (float4 *)c->rel);
+                                                     (float4 *)c->rel, c->block_box);
     else
         k_permute<double4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                       c->pid, c->pos_alt, c->mom_alt,
-                                                      c->pid_alt, (double4 *)c->rel);
+                                                      c->pid_alt, (double4 *)c->rel, c->block_box);
     double *t = c->pos;
     c->pos = c->pos_alt;
     c->pos_alt = t;
@@ -420,6 +475,18 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     cudaError_t e = launch_scan_u32(c->work_off, c->work_off, (size_t)c->g.n_cells + 1,
                                     c->scan_aux, c->stream);
     if (e != cudaSuccess) return e;
-    k_work_fill<<<gc, 256, 0, c->stream>>>(c->cell_start, c->work_off, c->g.n_cells, c->work);
-    return cudaGetLastError();
+    cudaMemsetAsync(c->work_key, 0xFF, sizeof(uint32_t) * c->max_work, c->stream);
+    k_work_fill<<<gc, 256, 0, c->stream>>>(c->cell_start, c->work_off, c->g.n_c, c->work,
+                                           c->work_key, c->work_order);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // most expensive work items first (longest-processing-time order for the pair kernel)
+    uint32_t *k[2] = {c->work_key, c->work_key_alt}, *v[2] = {c->work_order, c->work_order_alt};
+    e = radix_sort_pairs(k, v, false, (int64_t)c->max_work, 16, c->digit_counts, c->scan_aux,
+                         c->stream, &c->launches);
+    c->work_key = k[0];
+    c->work_key_alt = k[1];
+    c->work_order = v[0];
+    c->work_order_alt = v[1];
+    return e;
 }

@@ -50,6 +50,7 @@ def test_default_options_and_phase_names(lib):
     ((64.0, 32768, 32, 1.25, 4.5), None),            # valid -> reaches the device query
     ((64.0, 32768, 31, 1.25, 4.5), "mesh"),          # odd mesh
     ((64.0, 0, 32, 1.25, 4.5), "n must"),            # empty particle set
+    ((64.0, 1 << 31, 32, 1.25, 4.5), "n must"),      # too many particles
     ((-1.0, 100, 32, 1.25, 4.5), "box"),
     ((20.0, 100, 16, 1.25, 4.5), "chaining cells"),  # r_c too large: n_c = 2 < 3
     ((64.0, 100, 32, 0.0, 4.5), "r_s"),
