@@ -163,8 +163,9 @@ def run_ours(args, rank, world, local_rank, dist):
     n = w["n_p"] ** 3
     seed = w["seed"] + rank
     pos0, mom0 = S.zeldovich(w["n_p"], w["box"], w["a_begin"], seed)
+    extra = {} if args.sub_bits is None else {"sub_bits": args.sub_bits}
     sim = P3M(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"], softening=w["softening"],
-              precision=args.precision, stream=stream)
+              precision=args.precision, stream=stream, **extra)
     sim.set_particles(pos0, mom0, a=w["a_begin"])
     a_s = S.log_spaced_steps(w["a_begin"], w["a_end"], w["setup_steps"])
     t_setup = time.perf_counter()
@@ -267,7 +268,7 @@ def run_ours(args, rank, world, local_rank, dist):
            "dtype": "f32 forces, f64 positions/momenta" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD_NAME, "particles": n, "mesh": M,
-                      "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                      "precision": args.precision, "sub_bits": sim.geometry()["sub_bits"], "parallelism": "replicas" if world > 1 else "single",
                       "l2": "per-step working set (~0.5 GB) larger than L2; no flush",
                       "setup_s": t_setup},
            "roofline": roofline, "kernels": kernels,
@@ -405,6 +406,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--sub-bits", type=int, default=None,
+                    help="Morton bits per axis inside a chaining cell (library default if unset)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=20000,

@@ -77,8 +77,9 @@ typedef struct {
     int deconvolve_cic; /* 1 (default): divide G(k) by W(k)^2                              */
     int short_range;    /* 1 (default): P3M; 0: pure PM ('PM' kick algorithm: no Gaussian
                            filter, no pair sum)                                             */
-    int sub_bits;       /* b in 0..2: each chaining cell is split 2^b per side in the sort key
-                           (Morton order inside the cell); -1 = default (2)                */
+    int sub_bits;       /* b in 0..3: each chaining cell is split 2^b per side in the sort key
+                           (Morton order inside the cell); -1 = default (2).  The key
+                           (n_c^3 << 3b) must fit in 32 bits                               */
     void *stream;       /* cudaStream_t for all work of the context; NULL = legacy stream  */
 } p3m_options;
 

@@ -338,7 +338,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         return fail(c, P3M_EINVAL, "p3m_init: unknown precision mode");
     if (!(opt.softening >= 0.0) || !isfinite(opt.softening))
         return fail(c, P3M_EINVAL, "p3m_init: softening must be >= 0");
-    if (opt.sub_bits > 2) return fail(c, P3M_EINVAL, "p3m_init: sub_bits must be in 0..2");
+    if (opt.sub_bits > 3) return fail(c, P3M_EINVAL, "p3m_init: sub_bits must be in 0..3");
     if (!finite_pos(cs.omega_m) || !(cs.omega_lambda >= 0.0) || !isfinite(cs.omega_lambda))
         return fail(c, P3M_EINVAL, "p3m_init: need omega_m > 0 and omega_lambda >= 0");
 
