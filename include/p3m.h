@@ -201,6 +201,38 @@ int p3m_timings(p3m_ctx *ctx, double *ms, int n, int reset);
  * "fft_c2r", "gather", "pairs", "other"), or NULL. */
 const char *p3m_phase_name(int i);
 
+/*
+ * Allocation-free cell binning.  The paper has no counterpart to this entry point: it serves
+ * callers that may not allocate GPU memory themselves.  Examples are code embedded in a
+ * framework whose own caching allocator owns the device memory (a cudaMalloc behind its back
+ * escapes its accounting and fragments its pool), or a time-critical loop that cannot accept
+ * cudaMalloc's device synchronisation and unpredictable latency.  p3m_init allocates; this
+ * call does not.
+ *
+ * From caller-owned device arrays it computes what p3m_get_cells reports after a force
+ * evaluation of a context with the same box, n_c and sub_bits:
+ *   pos3n          [3][n] doubles on the device (not modified; wrapped into [0, box) for
+ *                  the keys only)
+ *   keys_out[n], ids_out[n], cell_start_out[n_c^3 + 1]   uint32 device arrays, caller-owned
+ *   n_c            chaining cells per side (p3m_get_geometry of a context gives it)
+ *   stream         cudaStream_t (NULL: legacy stream); the results are ready when the stream
+ *                  reaches the end of the call's work
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its temporary storage is one
+ * fixed area of about 12.3 MiB that the library reserves in the GPU's global memory when it
+ * is loaded.  Every GPU that loads the library holds that area until the process exits, and
+ * it bounds n to at most P3M_NOALLOC_MAX_N particles.  Larger n, NULL pointers or an invalid
+ * geometry return P3M_EINVAL before any launch, with the reason in p3m_last_error(NULL).
+ * The first call on each device performs a one-time set-up (it looks up the device address of
+ * that area with the device current); make that first call before any stream capture begins.
+ * All calls share the one area, which keeps the contents of the last call (nothing in it needs
+ * to start at zero): calls whose GPU work overlaps, on different streams or from different
+ * host threads, race and corrupt each other's results.  Order them on one stream.
+ */
+#define P3M_NOALLOC_MAX_N 1048576
+int p3m_cell_sort_noalloc(const double *pos3n, int64_t n, double box, int n_c, int sub_bits,
+                          uint32_t *keys_out, uint32_t *ids_out, uint32_t *cell_start_out,
+                          void *stream);
+
 /* Message of the last failure on ctx (ctx NULL: the last failed p3m_init).  Never NULL. */
 const char *p3m_last_error(const p3m_ctx *ctx);
 

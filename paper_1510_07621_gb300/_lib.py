@@ -23,6 +23,7 @@ P3M_ENONFINITE = -7
 P3M_PREC_MIXED = 0
 P3M_PREC_FP64 = 1
 P3M_NPHASES = 10
+P3M_NOALLOC_MAX_N = 1048576
 
 # every symbol the header declares, with (restype, argtypes)
 _c = ctypes
@@ -66,6 +67,8 @@ SIGNATURES = {
     "p3m_set_timing": (_c.c_int, [_vp, _c.c_int]),
     "p3m_timings": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.c_int, _c.c_int]),
     "p3m_phase_name": (_c.c_char_p, [_c.c_int]),
+    "p3m_cell_sort_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_double, _c.c_int, _c.c_int,
+                                         _vp, _vp, _vp, _vp]),
     "p3m_last_error": (_c.c_char_p, [_vp]),
     "p3m_free": (None, [_vp]),
 }

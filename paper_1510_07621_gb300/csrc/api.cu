@@ -287,6 +287,15 @@ bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
 }  // namespace
 
+int p3m_fail_global(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_init_err, sizeof(g_init_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
 // ---------------------------------------------------------------- host cosmology helpers
 
 double p3m_kick_factor(const p3m_cosmology &cs, double a1, double a2)

@@ -133,5 +133,7 @@ cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst);
 cudaError_t launch_diag(p3m_ctx *c, double *host_out /* [4]: px py pz 2*kinetic*m*a^2 */);
 
 // host helpers (api.cu)
+// Records a message for p3m_last_error(NULL) and returns code.
+int p3m_fail_global(int code, const char *fmt, ...);
 double p3m_kick_factor(const p3m_cosmology &cs, double a1, double a2);
 double p3m_drift_factor(const p3m_cosmology &cs, double a1, double a2);

@@ -9,6 +9,10 @@
 // Particles are ordered by key, ties by their current slot (a stable sort), so the order is
 // reproducible bit for bit.
 #include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "p3m_internal.cuh"
 
@@ -489,4 +493,120 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     c->work_order = v[0];
     c->work_order_alt = v[1];
     return e;
+}
+
+// ------------------------------------------------------------------ allocation-free binning
+// p3m_cell_sort_noalloc: the chaining-cell keys, stable sort and cell ranges of the context's
+// force evaluation, for callers that must not allocate device memory.  Its scratch (two key
+// arrays, the spare value array, the radix digit counts and the scan partials) is one
+// file-scope device array, sized for at most P3M_NOALLOC_MAX_N particles; every GPU that loads
+// the library holds it until the process exits.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = P3M_NOALLOC_MAX_N;
+constexpr int kNoAllocTiles = (int)((kNoAllocMaxN + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
+constexpr size_t kNoAllocCounts = (size_t)kRadix * kNoAllocTiles;
+constexpr size_t kNoAllocAux = kNoAllocCounts / P3M_SORT_TILE + 8;
+constexpr size_t kNoAllocWords = 3 * (size_t)kNoAllocMaxN + kNoAllocCounts + kNoAllocAux;
+
+// Keys of positions that stay unmodified: the same wrap and key arithmetic as
+// k_kick_drift_keys, without writing the positions back.
+__global__ void k_keys_only(const double *__restrict__ pos, P3MGeom g, uint32_t *__restrict__ keys)
+{
+    const int64_t n = g.n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t f[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) f[d] = fine_index(wrap_box(pos[d * n + i], g.box), g.inv_fine, g.n_fine);
+        keys[i] = make_key(f[0], f[1], f[2], g);
+    }
+}
+
+}  // namespace
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+uint32_t *g_noalloc_ptr[256];  // device address of g_noalloc_scratch, per device ordinal
+
+// Device address of the scratch on the current device.  Looked up with the device current,
+// once per device; the host-side symbol itself is not a device address.
+cudaError_t noalloc_scratch(uint32_t **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (uint32_t *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int p3m_cell_sort_noalloc(const double *pos3n, int64_t n, double box, int n_c,
+                                     int sub_bits, uint32_t *keys_out, uint32_t *ids_out,
+                                     uint32_t *cell_start_out, void *stream)
+{
+    if (!pos3n || !keys_out || !ids_out || !cell_start_out)
+        return p3m_fail_global(P3M_EINVAL, "p3m_cell_sort_noalloc: NULL pointer argument");
+    if (n < 1 || n > kNoAllocMaxN)
+        return p3m_fail_global(P3M_EINVAL,
+                               "p3m_cell_sort_noalloc: n = %lld outside [1, %lld] (fixed scratch size)",
+                               (long long)n, (long long)kNoAllocMaxN);
+    if (!(box > 0.0) || !isfinite(box) || n_c < 1 || n_c > 1024 || sub_bits < 0 || sub_bits > 3)
+        return p3m_fail_global(P3M_EINVAL, "p3m_cell_sort_noalloc: need box > 0, 1 <= n_c <= 1024, "
+                                           "0 <= sub_bits <= 3");
+    const uint64_t max_key = ((uint64_t)n_c * n_c * n_c << (3 * sub_bits)) - 1;
+    if (max_key >= (1ull << 32))
+        return p3m_fail_global(P3M_EINVAL, "p3m_cell_sort_noalloc: sort key exceeds 32 bits");
+    int key_bits = 1;
+    while (key_bits < 32 && (max_key >> key_bits)) ++key_bits;
+
+    uint32_t *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess)
+        return p3m_fail_global(P3M_ECUDA, "p3m_cell_sort_noalloc: scratch lookup failed: %s",
+                               cudaGetErrorString(e));
+    uint32_t *keys0 = scratch, *keys1 = scratch + kNoAllocMaxN, *vals1 = scratch + 2 * kNoAllocMaxN;
+    uint32_t *counts = scratch + 3 * kNoAllocMaxN, *aux = counts + kNoAllocCounts;
+
+    P3MGeom g;
+    memset(&g, 0, sizeof(g));
+    g.box = box;
+    g.n = n;
+    g.n_c = n_c;
+    g.sub_bits = sub_bits;
+    g.n_fine = n_c << sub_bits;
+    g.inv_fine = (double)g.n_fine / box;
+    g.n_cells = n_c * n_c * n_c;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    k_keys_only<<<grid_for(n, 256, sms), 256, 0, s>>>(pos3n, g, keys0);
+    unsigned long long launches = 0;
+    uint32_t *k[2] = {keys0, keys1}, *v[2] = {ids_out, vals1};
+    e = radix_sort_pairs(k, v, true, n, key_bits, counts, aux, s, &launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(keys_out, k[0], 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && v[0] != ids_out)
+        e = cudaMemcpyAsync(ids_out, v[0], 4 * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+        k_cell_start<<<grid_for(n + 1, 256, sms), 256, 0, s>>>(keys_out, g, cell_start_out);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return p3m_fail_global(P3M_ECUDA, "p3m_cell_sort_noalloc: %s", cudaGetErrorString(e));
+    return P3M_OK;
 }
