@@ -98,6 +98,9 @@ typedef struct {
                              j particle (32 pair slots each): [0] in chunks entirely inside
                              r_c of every i of the warp, [1] in chunks tested pair by pair,
                              [2] tested ones that some i accepted                          */
+    uint64_t pair_blocks_culled; /* 32-particle j blocks skipped by the bounding-box test     */
+    uint64_t pair_tiles[2];  /* j tiles streamed through shared memory; [1] of them entirely
+                                culled                                                       */
     int64_t n;            /* number of particles                                            */
     int32_t n_cells_side; /* chaining cells per side n_c                                    */
     int32_t max_cell_count; /* most particles in one chaining cell (last sort)              */

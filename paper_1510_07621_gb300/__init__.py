@@ -165,6 +165,8 @@ class P3M:
         return {"momentum": np.array(d.momentum[:]), "kinetic": d.kinetic, "a": d.a,
                 "pairs": int(d.pairs), "pairs_total": int(d.pairs_total),
                 "launches": int(d.launches), "pair_warp_j": [int(v) for v in d.pair_warp_j],
+                "pair_blocks_culled": int(d.pair_blocks_culled),
+                "pair_tiles": [int(v) for v in d.pair_tiles],
                 "n": int(d.n), "n_cells_side": int(d.n_cells_side),
                 "max_cell_count": int(d.max_cell_count)}
 

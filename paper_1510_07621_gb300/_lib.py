@@ -45,7 +45,8 @@ class Diag(_c.Structure):
     _fields_ = [("momentum", _c.c_double * 3), ("kinetic", _c.c_double),
                 ("potential", _c.c_double), ("layzer_irvine", _c.c_double), ("a", _c.c_double),
                 ("pairs", _c.c_uint64), ("pairs_total", _c.c_uint64), ("launches", _c.c_uint64),
-                ("pair_warp_j", _c.c_uint64 * 3),
+                ("pair_warp_j", _c.c_uint64 * 3), ("pair_blocks_culled", _c.c_uint64),
+                ("pair_tiles", _c.c_uint64 * 2),
                 ("n", _c.c_int64), ("n_cells_side", _c.c_int32),
                 ("max_cell_count", _c.c_int32)]
 

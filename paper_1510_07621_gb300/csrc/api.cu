@@ -662,7 +662,7 @@ extern "C" int p3m_diagnostics(p3m_ctx *c, p3m_diag *out)
     out->momentum[1] = r[1];
     out->momentum[2] = r[2];
     out->kinetic = r[3] / (2.0 * c->mass * c->a * c->a);
-    unsigned long long pc[5] = {0, 0, 0, 0, 0};
+    unsigned long long pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t mc = 0;
     CK(cudaMemcpy(pc, c->pair_count, sizeof(pc), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&mc, c->counters + 2, sizeof(mc), cudaMemcpyDeviceToHost));
@@ -671,6 +671,9 @@ extern "C" int p3m_diagnostics(p3m_ctx *c, p3m_diag *out)
     out->pair_warp_j[0] = pc[2];
     out->pair_warp_j[1] = pc[3];
     out->pair_warp_j[2] = pc[4];
+    out->pair_blocks_culled = pc[5];
+    out->pair_tiles[0] = pc[6];
+    out->pair_tiles[1] = pc[7];
     out->launches = c->launches;
     out->max_cell_count = (int32_t)mc;
     return check_flags(c);

@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(32)
     }
     __syncwarp();
     uint32_t parity = 0u;  // bit b: parity of the next phase of bar[b]
-    unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0;
+    unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0, st_culled = 0,
+                       st_tiles = 0, st_empty_tiles = 0;
     bool timed_out = false;
 
     for (;;) {
@@ -284,14 +285,17 @@ __global__ void __launch_bounds__(32)
             const float cxs = (float)(xa - q.imx), cys = (float)(ya - q.imy), czs = (float)(za - q.imz);
             const V4 *tile = sj[buf];
             T px = 0, py = 0, pz = 0;
-            uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0;
+            uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0, n_culled = 0;
             for (uint32_t b = b_c; b < bend; ++b) {
                 const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
                 const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
                 const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
                 const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
                 const bool near = valid && ex * ex + ey * ey + ez * ez < rcull2;
-                if (!__any_sync(0xffffffffu, near)) continue;
+                if (!__any_sync(0xffffffffu, near)) {
+                    ++n_culled;
+                    continue;
+                }
                 // the block's slots that belong to the neighbour cell, as tile offsets
                 const uint32_t j0 = max(b * 32, nstart) - b_c * 32;
                 const uint32_t j1 = min(b * 32 + 32, nend) - b_c * 32;
@@ -349,6 +353,9 @@ __global__ void __launch_bounds__(32)
             st_fast += n_fast;
             st_tested += n_tested;
             st_eval += n_eval;
+            st_culled += n_culled;
+            ++st_tiles;
+            if (n_culled == bend - b_c) ++st_empty_tiles;
             buf ^= 1;
             nb_c = nb_n;
             b_c = b_n;
@@ -377,6 +384,9 @@ __global__ void __launch_bounds__(32)
         if (st_fast) atomicAdd(pair_count + 2, st_fast);
         if (st_tested) atomicAdd(pair_count + 3, st_tested);
         if (st_eval) atomicAdd(pair_count + 4, st_eval);
+        if (st_culled) atomicAdd(pair_count + 5, st_culled);
+        if (st_tiles) atomicAdd(pair_count + 6, st_tiles);
+        if (st_empty_tiles) atomicAdd(pair_count + 7, st_empty_tiles);
     }
 }
 
