@@ -78,7 +78,7 @@ typedef struct {
     int short_range;    /* 1 (default): P3M; 0: pure PM ('PM' kick algorithm: no Gaussian
                            filter, no pair sum)                                             */
     int sub_bits;       /* b in 0..3: each chaining cell is split 2^b per side in the sort key
-                           (Morton order inside the cell); -1 = default (2).  The key
+                           (Morton order inside the cell); -1 = default (3).  The key
                            (n_c^3 << 3b) must fit in 32 bits                               */
     void *stream;       /* cudaStream_t for all work of the context; NULL = legacy stream  */
 } p3m_options;

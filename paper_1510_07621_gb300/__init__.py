@@ -61,7 +61,7 @@ class P3M:
     def __init__(self, box: float, n: int, mesh: int, r_s_cells: float = 1.25,
                  cutoff: float = 4.5, omega_m: float = 1.0, omega_lambda: float = 0.0,
                  h0: float = 100.0, precision: str = "mixed", softening: float = 0.02,
-                 deconvolve: bool = True, short_range: bool = True, sub_bits: int = 2,
+                 deconvolve: bool = True, short_range: bool = True, sub_bits: int = 3,
                  stream=None):
         lib = load()
         self._lib = lib

@@ -319,7 +319,7 @@ extern "C" int p3m_default_options(p3m_options *opt)
     opt->softening = 0.02;
     opt->deconvolve_cic = 1;
     opt->short_range = 1;
-    opt->sub_bits = 2;
+    opt->sub_bits = 3;
     opt->stream = nullptr;
     return P3M_OK;
 }
@@ -333,7 +333,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
     p3m_options opt;
     p3m_default_options(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.sub_bits < 0) opt.sub_bits = 2;
+    if (opt.sub_bits < 0) opt.sub_bits = 3;
     p3m_cosmology cs = {1.0, 0.0, 100.0};
     if (cosmo) cs = *cosmo;
 

@@ -7,6 +7,7 @@
 // Spectrum layout (cuFFT R2C): M * M * (M/2+1) complex values, z fastest.
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <limits.h>
 
 #include "p3m_internal.cuh"
 
@@ -36,98 +37,116 @@ __device__ __forceinline__ void cic_stencil(double x, double inv_h, int &i0, T &
     f = (T)(u - fl);
 }
 
-// One CTA per chaining cell: the cell's particles accumulate into a W^3 node tile in shared
-// memory (tile origin one node below the cell's first node), which is then added to the mesh
-// with one global atomic per non-zero node.  Particles whose stencil leaves the tile (only
-// possible through rounding at the cell faces) go straight to the mesh.
+// Fixed-size chunks of the sorted particles (CTA b takes slots [b*1024, (b+1)*1024)), so that a
+// dense cell is spread over many CTAs.  The chunk's CIC nodes are accumulated in a shared-memory
+// tile spanning the chunk's node bounding box (found by a block reduction); the tile is then
+// added to the mesh with one global atomic per non-zero node.  A chunk whose box exceeds the
+// tile capacity (e.g. one that straddles the periodic boundary) adds straight to the mesh.
+constexpr int kDepChunk = 1024;
+constexpr int kDepTileMax = 4096;  // nodes
+
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_deposit_cells(const double *__restrict__ pos, const uint32_t *__restrict__ cell_start,
-                    P3MGeom g, int W, T *__restrict__ mesh)
+    k_deposit_chunks(const double *__restrict__ pos, P3MGeom g, T *__restrict__ mesh)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tile = reinterpret_cast<T *>(smem_raw);
-    const int M = g.mesh, nc = g.n_c, W3 = W * W * W;
+    __shared__ T tile[kDepTileMax];
+    __shared__ int s_lo[3][8], s_hi[3][8];
+    const int M = g.mesh;
     const int64_t n = g.n;
-    for (int cell = blockIdx.x; cell < g.n_cells; cell += gridDim.x) {
-        const uint32_t s = cell_start[cell], e = cell_start[cell + 1];
-        if (s == e) continue;
-        const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
-        const int ox = (int)((int64_t)cx * M / nc) - 1;
-        const int oy = (int)((int64_t)cy * M / nc) - 1;
-        const int oz = (int)((int64_t)cz * M / nc) - 1;
-        for (int t = threadIdx.x; t < W3; t += blockDim.x) tile[t] = T(0);
-        __syncthreads();
-        for (uint32_t k = s + threadIdx.x; k < e; k += blockDim.x) {
-            int ix, iy, iz;
-            T fx, fy, fz;
-            cic_stencil(pos[k], g.inv_h, ix, fx);
-            cic_stencil(pos[n + k], g.inv_h, iy, fy);
-            cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
-            const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
-            const int lx = ix - ox, ly = iy - oy, lz = iz - oz;
-            if (lx >= 0 && lx + 1 < W && ly >= 0 && ly + 1 < W && lz >= 0 && lz + 1 < W) {
+    const int64_t base = (int64_t)blockIdx.x * kDepChunk;
+    const int per = kDepChunk / 256;
+    int i0[4][3];
+    T f[4][3];
+    bool act[4];
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
 #pragma unroll
-                for (int a = 0; a < 2; ++a)
+    for (int r = 0; r < per; ++r) {
+        const int64_t k = base + r * 256 + threadIdx.x;
+        act[r] = k < n;
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const T wab = wx[a] * wy[b];
-                        T *row = tile + ((lx + a) * W + (ly + b)) * W + lz;
-                        atomicAdd(row, wab * wz[0]);
-                        atomicAdd(row + 1, wab * wz[1]);
-                    }
+        for (int d = 0; d < 3; ++d) {
+            if (act[r]) {
+                cic_stencil(pos[d * n + k], g.inv_h, i0[r][d], f[r][d]);
+                lo[d] = min(lo[d], i0[r][d]);
+                hi[d] = max(hi[d], i0[r][d] + 1);
             } else {
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int b = 0; b < 2; ++b)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            const size_t node = ((size_t)wrap_index(ix + a, M) * M +
-                                                 wrap_index(iy + b, M)) * M + wrap_index(iz + c, M);
-                            atomicAdd(mesh + node, wx[a] * wy[b] * wz[c]);
-                        }
+                i0[r][d] = 0;
+                f[r][d] = T(0);
             }
         }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+        if (lane == 0) {
+            s_lo[d][warp] = lo[d];
+            s_hi[d][warp] = hi[d];
+        }
+    }
+    __syncthreads();
+    int blo[3], bdim[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int a = INT_MAX, b = INT_MIN;
+        for (int w = 0; w < 8; ++w) {
+            a = min(a, s_lo[d][w]);
+            b = max(b, s_hi[d][w]);
+        }
+        blo[d] = a;
+        bdim[d] = b - a + 1;
+    }
+    const long long vol = (long long)bdim[0] * bdim[1] * bdim[2];
+    if (vol <= kDepTileMax) {
+        for (int t = threadIdx.x; t < vol; t += 256) tile[t] = T(0);
         __syncthreads();
-        for (int t = threadIdx.x; t < W3; t += blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < per; ++r) {
+            if (!act[r]) continue;
+            const int lx = i0[r][0] - blo[0], ly = i0[r][1] - blo[1], lz = i0[r][2] - blo[2];
+            const T wx[2] = {T(1) - f[r][0], f[r][0]}, wy[2] = {T(1) - f[r][1], f[r][1]};
+            const T wz[2] = {T(1) - f[r][2], f[r][2]};
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const T wab = wx[a] * wy[b];
+                    T *row = tile + ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
+                    atomicAdd(row, wab * wz[0]);
+                    atomicAdd(row + 1, wab * wz[1]);
+                }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < vol; t += 256) {
             const T v = tile[t];
             if (v != T(0)) {
-                const int lz = t % W, ly = (t / W) % W, lx = t / (W * W);
-                const size_t node = ((size_t)wrap_index(ox + lx, M) * M + wrap_index(oy + ly, M)) * M +
-                                    wrap_index(oz + lz, M);
+                const int lz = t % bdim[2], ly = (t / bdim[2]) % bdim[1], lx = t / (bdim[2] * bdim[1]);
+                const size_t node = ((size_t)wrap_index(blo[0] + lx, M) * M + wrap_index(blo[1] + ly, M)) * M +
+                                    wrap_index(blo[2] + lz, M);
                 atomicAdd(mesh + node, v);
             }
         }
-        __syncthreads();
-    }
-}
-
-// Fallback when a cell's node tile does not fit in shared memory: one global atomic per
-// stencil node.
-template <typename T>
-__global__ void k_deposit_direct(const double *__restrict__ pos, P3MGeom g, T *__restrict__ mesh)
-{
-    const int M = g.mesh;
-    const int64_t n = g.n;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        int ix, iy, iz;
-        T fx, fy, fz;
-        cic_stencil(pos[k], g.inv_h, ix, fx);
-        cic_stencil(pos[n + k], g.inv_h, iy, fy);
-        cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
-        const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
+    } else {
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int r = 0; r < per; ++r) {
+            if (!act[r]) continue;
+            const T wx[2] = {T(1) - f[r][0], f[r][0]}, wy[2] = {T(1) - f[r][1], f[r][1]};
+            const T wz[2] = {T(1) - f[r][2], f[r][2]};
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const size_t node = ((size_t)wrap_index(ix + a, M) * M + wrap_index(iy + b, M)) * M +
-                                        wrap_index(iz + c, M);
-                    atomicAdd(mesh + node, wx[a] * wy[b] * wz[c]);
-                }
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const size_t node = ((size_t)wrap_index(i0[r][0] + a, M) * M +
+                                             wrap_index(i0[r][1] + b, M)) * M + wrap_index(i0[r][2] + c, M);
+                        atomicAdd(mesh + node, wx[a] * wy[b] * wz[c]);
+                    }
+        }
     }
 }
 
@@ -216,15 +235,8 @@ cudaError_t deposit_impl(p3m_ctx *c)
     T *mesh = (T *)c->rho;
     c->launches += 2;  // fill, deposit
     k_fill<T><<<grid_for(M3, 256, c->num_sms), 256, 0, c->stream>>>(mesh, M3, (T)(-c->g.mean_count));
-    const int W = (c->g.mesh + c->g.n_c - 1) / c->g.n_c + 4;
-    const size_t smem = (size_t)W * W * W * sizeof(T);
-    if (smem <= 48 * 1024) {
-        const int grid = c->g.n_cells < c->num_sms * 8 ? c->g.n_cells : c->num_sms * 8;
-        k_deposit_cells<T><<<grid, 256, smem, c->stream>>>(c->pos, c->cell_start, c->g, W, mesh);
-    } else {
-        k_deposit_direct<T><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(c->pos, c->g,
-                                                                                       mesh);
-    }
+    const int64_t chunks = (c->g.n + kDepChunk - 1) / kDepChunk;
+    k_deposit_chunks<T><<<(unsigned)chunks, 256, 0, c->stream>>>(c->pos, c->g, mesh);
     return cudaGetLastError();
 }
 

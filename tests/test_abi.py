@@ -39,7 +39,7 @@ def test_default_options_and_phase_names(lib):
     opt = _lib.Options()
     assert lib.p3m_default_options(ctypes.byref(opt)) == 0
     assert opt.precision == _lib.P3M_PREC_MIXED and opt.short_range == 1
-    assert abs(opt.softening - 0.02) < 1e-15 and opt.sub_bits == 2
+    assert abs(opt.softening - 0.02) < 1e-15 and opt.sub_bits == 3
     assert lib.p3m_default_options(None) == _lib.P3M_EINVAL
     names = [lib.p3m_phase_name(i).decode() for i in range(_lib.P3M_NPHASES)]
     assert names[0] == "kick_drift" and names[8] == "pairs"
