@@ -166,6 +166,23 @@ int p3m_step(p3m_ctx *ctx, double a, double da);
 int p3m_get_particles(p3m_ctx *ctx, double *pos3n, double *mom3n, double *acc3n,
                       int on_device);
 
+/*
+ * Power spectrum of the current particle distribution on the PM mesh (Ch. Parameters:
+ * PM_gridsize is also the power-spectrum grid, R_tophat the radius of the top-hat sphere for
+ * sigma; Ch. Tests: powerspec).  delta = n/n_bar - 1 on the CIC count mesh, delta_k its DFT
+ * divided by M^3; shell b (0 <= b < n_bins <= M/2) holds the modes with round(|k|/k_f) = b+1,
+ * k_f = 2 pi / box:
+ *   k_mean[b]  mean |k| of the shell's modes     power[b]  box^3 <|delta_k|^2 / W(k)^2>
+ *   n_modes[b] number of modes (both halves of the spectrum)
+ * W(k)^2 = prod_d sinc^4(k_d h/2) when deconvolve != 0, else 1; shot noise is not subtracted.
+ * sigma (nullable): with tophat_radius R > 0, sigma_R = sqrt(sum_{k != 0} |delta_k|^2 / W^2
+ * W_TH(k R)^2), W_TH(x) = 3 (sin x - x cos x) / x^3.  Output arrays are host arrays (each
+ * nullable); synchronises.  Overwrites the density mesh of p3m_get_mesh(0) with the current
+ * positions.  Errors: P3M_EINVAL, P3M_ESTATE, P3M_ECUDA, P3M_ECUFFT.
+ */
+int p3m_power_spectrum(p3m_ctx *ctx, int n_bins, int deconvolve, double tophat_radius,
+                       double *k_mean, double *power, double *n_modes, double *sigma);
+
 /* Momentum, kinetic energy, pair count and cell statistics of the current state.
  * Synchronises the stream. */
 int p3m_diagnostics(p3m_ctx *ctx, p3m_diag *out);

@@ -260,7 +260,7 @@ def pm_force_meshes(pos: np.ndarray, p: Params):
     phik = green(p) * rk
     gx, gy, gz = gradient_wavenumbers(p)
     GX, GY, GZ = np.meshgrid(gx, gy, gz, indexing="ij")
-    return [np.fft.irfftn(-1j * K * phik, s=(M, M, M)) for K in (GX, GY, GZ)], rho
+    return [np.fft.irfftn(-1j * K * phik, s=(M, M, M), axes=(0, 1, 2)) for K in (GX, GY, GZ)], rho
 
 
 def pm_accel(pos: np.ndarray, p: Params, targets=None) -> np.ndarray:
@@ -468,3 +468,77 @@ def momentum(mom: np.ndarray) -> np.ndarray:
 def kinetic_energy(mom: np.ndarray, a: float, mass: float = 1.0) -> float:
     """Peculiar kinetic energy sum_i |p_i|^2 / (2 m a^2)."""
     return float(np.sum(mom * mom) / (2.0 * mass * a * a))
+
+
+# --------------------------------------------------------------------------- power spectrum
+# Ch. Parameters: PM_gridsize is also the grid of the power spectrum, and R_tophat the radius
+# of the top-hat sphere for sigma (the rms density variation) computed from the power spectrum.
+# Readings: delta = n/n_bar - 1 on the CIC count mesh; delta_k = DFT(delta)/M^3;
+# P(k) = L^3 <|delta_k|^2 / W(k)^2> over a shell (the deconvolution optional, no shot-noise
+# subtraction); shell b holds the modes with round(|k|/k_f) = b + 1, k_f = 2 pi / L, up to
+# b + 1 = M/2; sigma_R^2 = sum over all k != 0 of |delta_k|^2 / W(k)^2 * W_TH(k R)^2 with
+# W_TH(x) = 3 (sin x - x cos x) / x^3.
+
+
+def tophat_window(x):
+    """Fourier transform of the unit top-hat sphere, 3 (sin x - x cos x) / x^3, W(0) = 1."""
+    x = np.asarray(x, dtype=np.float64)
+    small = np.abs(x) < 1e-3
+    xs = np.where(small, 1.0, x)
+    w = 3.0 * (np.sin(xs) - xs * np.cos(xs)) / xs ** 3
+    return np.where(small, 1.0 - x * x / 10.0, w)
+
+
+def power_from_mesh(delta: np.ndarray, box: float, deconvolve: bool = True, radius: float = 0.0):
+    """Binned power spectrum of a density-contrast mesh (M, M, M): returns (k_mean, P, n_modes,
+    sigma_R) with the full complex transform (every mode counted once)."""
+    M = delta.shape[0]
+    dk = np.fft.fftn(delta) / M ** 3
+    k1 = 2.0 * np.pi * np.fft.fftfreq(M, d=box / M)
+    KX, KY, KZ = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(KX * KX + KY * KY + KZ * KZ)
+    p2 = np.abs(dk) ** 2
+    if deconvolve:
+        h = box / M
+
+        def sinc(k):
+            x = 0.5 * k * h
+            return np.where(x == 0.0, 1.0, np.sin(x) / np.where(x == 0.0, 1.0, x))
+        p2 = p2 / (sinc(KX) * sinc(KY) * sinc(KZ)) ** 4
+    kf = 2.0 * np.pi / box
+    shell = np.floor(kk / kf + 0.5).astype(np.int64) - 1
+    nb = M // 2
+    sel = (shell >= 0) & (shell < nb)
+    cnt = np.bincount(shell[sel], minlength=nb).astype(np.float64)
+    psum = np.bincount(shell[sel], weights=p2[sel], minlength=nb)
+    ksum = np.bincount(shell[sel], weights=kk[sel], minlength=nb)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        kmean = ksum / cnt
+        power = box ** 3 * psum / cnt
+    sigma = None
+    if radius > 0.0:
+        nz = kk > 0
+        sigma = float(np.sqrt(np.sum(p2[nz] * tophat_window(kk[nz] * radius) ** 2)))
+    return kmean, power, cnt, sigma
+
+
+def power_spectrum(pos: np.ndarray, p: Params, deconvolve: bool = True, radius: float = 0.0):
+    """Power spectrum of a particle set: CIC counts -> delta = n / n_bar - 1 -> power_from_mesh."""
+    n = cic_deposit(wrap(pos, p.box), p)
+    nbar = pos.shape[1] / p.mesh ** 3
+    return power_from_mesh(n / nbar - 1.0, p.box, deconvolve, radius)
+
+
+def cic_shot_noise(k_vec_index, p: Params, n_particles: int, deconvolve: bool = True):
+    """Expected power of a Poisson particle set after CIC assignment (Jing 2005, ApJ 620, 559):
+    P_shot(k) = (L^3/N) prod_d [1 - (2/3) sin^2(k_d h / 2)], divided by W(k)^2 when
+    deconvolved.  k_vec_index: integer mode vectors (3, m)."""
+    h = p.h
+    k = (2.0 * np.pi / p.box) * np.asarray(k_vec_index, dtype=np.float64)
+    s2 = np.sin(0.5 * k * h) ** 2
+    ps = (p.box ** 3 / n_particles) * np.prod(1.0 - (2.0 / 3.0) * s2, axis=0)
+    if deconvolve:
+        x = 0.5 * k * h
+        sinc = np.where(x == 0.0, 1.0, np.sin(x) / np.where(x == 0.0, 1.0, x))
+        ps = ps / np.prod(sinc, axis=0) ** 4
+    return ps

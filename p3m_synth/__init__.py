@@ -108,7 +108,7 @@ def zeldovich(n_p: int, box: float, a_begin: float, seed: int, rms_cells: float 
     psi = []
     for kd in (kx, ky, kz):
         kd_g = np.where(np.isclose(np.abs(kd), nyq), 0.0, kd)
-        psi.append(np.fft.irfftn(1j * kd_g * dk * inv_k2, s=(n, n, n)).ravel())
+        psi.append(np.fft.irfftn(1j * kd_g * dk * inv_k2, s=(n, n, n), axes=(0, 1, 2)).ravel())
     psi = np.stack(psi)
     rms = np.sqrt(np.mean(np.sum(psi * psi, axis=0)))
     psi *= rms_cells * (box / n) / rms

@@ -158,6 +158,19 @@ class P3M:
     def step(self, a: float, da: float):
         self._check(self._lib.p3m_step(self._ctx, float(a), float(da)))
 
+    def power_spectrum(self, n_bins: int | None = None, deconvolve: bool = True,
+                       tophat_radius: float = 0.0):
+        """(k_mean, power, n_modes, sigma) of the current positions; see p3m_power_spectrum."""
+        nb = self.mesh // 2 if n_bins is None else int(n_bins)
+        k = np.empty(nb)
+        p = np.empty(nb)
+        c = np.empty(nb)
+        s = ctypes.c_double(float("nan"))
+        self._check(self._lib.p3m_power_spectrum(self._ctx, nb, 1 if deconvolve else 0,
+                                                 float(tophat_radius), k.ctypes.data,
+                                                 p.ctypes.data, c.ctypes.data, ctypes.byref(s)))
+        return k, p, c, (s.value if tophat_radius > 0 else None)
+
     # ------------------------------------------------------------------ introspection
     def diagnostics(self) -> dict:
         d = Diag()

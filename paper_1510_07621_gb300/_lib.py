@@ -59,6 +59,8 @@ SIGNATURES = {
     "p3m_forces": (_c.c_int, [_vp, _c.c_double, _dp, _c.c_int]),
     "p3m_forces_split": (_c.c_int, [_vp, _dp, _dp, _c.c_int]),
     "p3m_step": (_c.c_int, [_vp, _c.c_double, _c.c_double]),
+    "p3m_power_spectrum": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_double, _vp, _vp, _vp,
+                                      _c.POINTER(_c.c_double)]),
     "p3m_get_particles": (_c.c_int, [_vp, _dp, _dp, _dp, _c.c_int]),
     "p3m_diagnostics": (_c.c_int, [_vp, _c.POINTER(Diag)]),
     "p3m_get_cells": (_c.c_int, [_vp, _vp, _vp, _vp, _c.c_int]),

@@ -185,7 +185,8 @@ void release(p3m_ctx *c)
                     c->cell_start, c->work,    c->work_off,     c->counters, c->pair_count,
                     c->red,       c->rho,      c->rho_k,        c->frc_k,    c->frc,
                     c->tab_k,     c->tab_kg,   c->tab_g,        c->work_key, c->work_key_alt,
-                    c->work_order, c->work_order_alt, c->block_box};
+                    c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
+                    c->tab_one,   c->ps_acc};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -436,7 +437,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->rho, real * M3},    {(void **)&c->rho_k, 2 * real * nk},
             {(void **)&c->frc_k, 6 * real * nk}, {(void **)&c->frc, 3 * real * M3},
             {(void **)&c->tab_k, real * M},   {(void **)&c->tab_kg, real * M},
-            {(void **)&c->tab_g, real * M},
+            {(void **)&c->tab_g, real * M},   {(void **)&c->tab_invw2, 8 * M},
+            {(void **)&c->tab_one, 8 * M},    {(void **)&c->ps_acc, 8 * (3 * (M / 2) + 1)},
         };
         for (auto &a : allocs) {
             e = dalloc(a.p, a.bytes);
@@ -481,6 +483,16 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             e = cudaMemcpy(c->tab_k, tk.data(), 8 * M, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(c->tab_kg, tkg.data(), 8 * M, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(c->tab_g, tg.data(), 8 * M, cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) {
+            std::vector<double> w2(M), one(M, 1.0);
+            for (int i = 0; i < mesh; ++i) {
+                const double x = 0.5 * tk[i] * h;
+                const double s = x == 0.0 ? 1.0 : sin(x) / x;
+                w2[i] = 1.0 / ((s * s) * (s * s));
+            }
+            e = cudaMemcpy(c->tab_invw2, w2.data(), 8 * M, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->tab_one, one.data(), 8 * M, cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
             rc = fail(nullptr, P3M_ECUDA, "p3m_init: table upload failed: %s", cudaGetErrorString(e));
@@ -621,6 +633,36 @@ extern "C" int p3m_step(p3m_ctx *c, double a, double da)
     rc = evaluate(c, k2, nullptr);
     if (rc) return rc;
     c->a = a2;
+    return P3M_OK;
+}
+
+extern "C" int p3m_power_spectrum(p3m_ctx *c, int n_bins, int deconvolve, double tophat_radius,
+                                  double *k_mean, double *power, double *n_modes, double *sigma)
+{
+    if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_power_spectrum: no particles loaded");
+    const int nb_max = c->g.mesh / 2;
+    if (n_bins < 1 || n_bins > nb_max)
+        return fail(c, P3M_EINVAL, "p3m_power_spectrum: n_bins must be in [1, %d]", nb_max);
+    if (!(tophat_radius >= 0.0) || !isfinite(tophat_radius))
+        return fail(c, P3M_EINVAL, "p3m_power_spectrum: tophat_radius must be >= 0");
+    CK(launch_deposit(c));
+    CKF(c->precision == P3M_PREC_MIXED
+            ? cufftExecR2C(c->plan_r2c, (cufftReal *)c->rho, (cufftComplex *)c->rho_k)
+            : cufftExecD2Z(c->plan_r2c, (cufftDoubleReal *)c->rho, (cufftDoubleComplex *)c->rho_k));
+    CK(launch_powspec(c, deconvolve ? c->tab_invw2 : c->tab_one, sigma ? tophat_radius : 0.0, n_bins,
+                      c->ps_acc));
+    std::vector<double> h(3 * (size_t)n_bins + 1);
+    CK(cudaMemcpyAsync(h.data(), c->ps_acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double L3 = c->g.box * c->g.box * c->g.box;
+    for (int b = 0; b < n_bins; ++b) {
+        const double cnt = h[3 * b + 2];
+        if (k_mean) k_mean[b] = cnt > 0 ? h[3 * b + 1] / cnt : NAN;
+        if (power) power[b] = cnt > 0 ? L3 * h[3 * b] / cnt : NAN;
+        if (n_modes) n_modes[b] = cnt;
+    }
+    if (sigma) *sigma = tophat_radius > 0.0 ? sqrt(h[3 * n_bins]) : NAN;
     return P3M_OK;
 }
 

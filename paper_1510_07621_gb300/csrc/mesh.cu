@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <limits.h>
+#include <math.h>
 
 #include "p3m_internal.cuh"
 
@@ -220,6 +221,51 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Power spectrum binning over the R2C half spectrum of the count mesh minus its mean:
+// delta_k = rho_k / N; every mode (ix, iy, iz) stands for itself and, for 0 < iz < M/2, for its
+// conjugate partner (weight 2).  Shell b = round(|n|) - 1 accumulates w |delta_k|^2 / W^2,
+// w |k| and w; with radius > 0 the top-hat sum w |delta_k|^2 / W^2 W_TH(|k| R)^2 goes to
+// acc[3 n_bins].  Per-block shared-memory partial sums, then one FP64 atomic per bin.
+template <typename C2>
+__global__ void __launch_bounds__(256)
+    k_powspec(const C2 *__restrict__ rk, int M, const double *__restrict__ inv_w2, double kf,
+              double inv_n2, double radius, int n_bins, double *__restrict__ acc)
+{
+    extern __shared__ double sacc[];  // 3 * n_bins + 1
+    const int nacc = 3 * n_bins + 1;
+    for (int t = threadIdx.x; t < nacc; t += blockDim.x) sacc[t] = 0.0;
+    __syncthreads();
+    const int nz = M / 2 + 1;
+    const size_t total = (size_t)M * M * nz;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        if (idx == 0) continue;
+        const int iz = (int)(idx % nz);
+        const size_t t = idx / nz;
+        const int iy = (int)(t % M), ix = (int)(t / M);
+        const int sx = ix <= M / 2 ? ix : ix - M, sy = iy <= M / 2 ? iy : iy - M;
+        const double w = (iz == 0 || iz == M / 2) ? 1.0 : 2.0;
+        const double nk = sqrt((double)sx * sx + (double)sy * sy + (double)iz * iz);
+        const C2 r = rk[idx];
+        const double p = ((double)r.x * r.x + (double)r.y * r.y) * inv_n2 * inv_w2[ix] * inv_w2[iy] *
+                         inv_w2[iz];
+        const int b = (int)floor(nk + 0.5) - 1;
+        if (b < n_bins) {
+            atomicAdd(&sacc[3 * b], w * p);
+            atomicAdd(&sacc[3 * b + 1], w * nk * kf);
+            atomicAdd(&sacc[3 * b + 2], w);
+        }
+        if (radius > 0.0) {
+            const double x = nk * kf * radius;
+            const double wt = x < 1e-3 ? 1.0 - x * x / 10.0 : 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
+            atomicAdd(&sacc[3 * n_bins], w * p * wt * wt);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nacc; t += blockDim.x)
+        if (sacc[t] != 0.0) atomicAdd(&acc[t], sacc[t]);
+}
+
 inline int grid_for(size_t n, int threads, int num_sms)
 {
     size_t b = (n + threads - 1) / threads;
@@ -265,6 +311,25 @@ cudaError_t launch_kspace(p3m_ctx *c)
             (const double *)c->tab_kg, (const double *)c->tab_g, M, c->green_const, f, f + nk,
             f + 2 * nk);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc)
+{
+    const int M = c->g.mesh;
+    const size_t nk = (size_t)M * M * (M / 2 + 1);
+    const size_t smem = sizeof(double) * (3 * (size_t)n_bins + 1);
+    const int grid = c->num_sms * 4;
+    const double kf = 2.0 * M_PI / c->g.box;
+    const double inv_n2 = 1.0 / ((double)c->g.n * (double)c->g.n);
+    c->launches += 1;
+    cudaMemsetAsync(acc, 0, smem, c->stream);
+    if (c->precision == P3M_PREC_MIXED)
+        k_powspec<cufftComplex><<<grid, 256, smem, c->stream>>>((const cufftComplex *)c->rho_k, M, inv_w2,
+                                                               kf, inv_n2, radius, n_bins, acc);
+    else
+        k_powspec<cufftDoubleComplex><<<grid, 256, smem, c->stream>>>(
+            (const cufftDoubleComplex *)c->rho_k, M, inv_w2, kf, inv_n2, radius, n_bins, acc);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,9 @@ struct p3m_ctx {
     // mesh (float or double)
     void *rho, *rho_k, *frc_k, *frc;
     void *tab_k, *tab_kg, *tab_g;  // per-axis |k|, gradient k, Green factor (length M)
+    double *tab_invw2;             // per-axis 1/sinc^4(k h/2) (FP64, length M)
+    double *tab_one;               // M ones (no deconvolution)
+    double *ps_acc;                // power spectrum partial sums (3 * (M/2) + 1)
     double green_const;
     float gpoly[12];  // FP32 split factor: g = 1 + x u Q(tau), Q = sum gpoly[k] tau^k (k <= 10),
                       // tau = u gpoly[11] - 1, u = (r/r_s)^2
@@ -118,6 +121,8 @@ cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_
 cudaError_t launch_deposit(p3m_ctx *c);
 cudaError_t launch_kspace(p3m_ctx *c);
 cudaError_t launch_gather(p3m_ctx *c, double *acc_out);
+// Bins the spectrum in c->rho_k into acc[3 n_bins + 1] (see k_powspec).
+cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc);
 
 // ------------------------------------------------------------------ launchers (pair.cu)
 // acc_out = acc_in + SR (acc_in NULL: SR only); kfac != 0: mom += kfac * acc_out.
