@@ -45,7 +45,8 @@ def test_power_spectrum_matches_oracle(P3M, case, precision, tol, deconvolve):
 
 
 def test_linear_growth_of_the_gpu_run(P3M):
-    """32^3 EdS run, 10 steps a = 0.02 -> 0.1: the largest scales grow as D(a)^2 = 25."""
+    """32^3 EdS run, 10 steps a = 0.02 -> 0.1: the two largest-scale shells grow as D(a)^2 = 25
+    (smaller scales are already nonlinear at a = 0.1, where the rms displacement is one cell)."""
     pos, mom = S.zeldovich(32, 64.0, 0.02, 1511)
     a_s = S.log_spaced_steps(0.02, 0.1, 10)
     with P3M(64.0, pos.shape[1], 32) as sim:
@@ -54,5 +55,5 @@ def test_linear_growth_of_the_gpu_run(P3M):
         for i in range(10):
             sim.step(a_s[i], a_s[i + 1] - a_s[i])
         _, P1, _, _ = sim.power_spectrum()
-    growth = P1[:3] / P0[:3]
-    assert np.all(np.abs(growth / 25.0 - 1.0) < 0.1), growth
+    growth = P1[:2] / P0[:2]
+    assert np.all(np.abs(growth / 25.0 - 1.0) < 0.05), growth
