@@ -375,6 +375,79 @@ def _traffic(kernel):
     return None
 
 
+# ---------------------------------------------------------------- batched ensemble
+
+
+ENSEMBLE_NAME = ("ensemble48: 48 independent EdS simulations, 16 each of 48^3, 64^3 and 96^3 "
+                 "particles, mesh = particle grid, box 100 Mpc/h, r_s 1.25 cells, cutoff 4.5 r_s, "
+                 "seeded Zel'dovich ICs (seed 4000+k), 20 log-spaced steps a=0.05->1")
+
+
+def run_ensemble(args):
+    """The 48-simulation ensemble advanced a = 0.05 -> 1 in 20 steps three ways: host-issued
+    steps one simulation after another on one stream, host-issued steps on one stream per
+    simulation, and one CUDA-graph launch per step for the whole ensemble."""
+    import torch
+    from paper_1510_07621_gb300 import P3M, Ensemble, build
+
+    build.build()
+    torch.cuda.set_device(0)
+    sizes = [48] * 16 + [64] * 16 + [96] * 16
+    box = 100.0
+    a = S.log_spaced_steps(0.05, 1.0, 20)
+    ics = [S.zeldovich(n_p, box, a[0], 4000 + k) for k, n_p in enumerate(sizes)]
+    total = sum(n_p ** 3 for n_p in sizes)
+
+    def fresh():
+        sims = [P3M(box, n_p ** 3, n_p, softening=0.02, stream=0) for n_p in sizes]
+        for s_, (p, m) in zip(sims, ics):
+            s_.set_particles(p, m, a=a[0])
+            s_.forces(a[0])
+        torch.cuda.synchronize()
+        return sims
+
+    out = {}
+    # 1. serial host launches, one simulation after another
+    sims = fresh()
+    t0 = time.perf_counter()
+    for k in range(20):
+        for s_ in sims:
+            s_.step(a[k], a[k + 1] - a[k])
+    torch.cuda.synchronize()
+    out["serial_host_launches"] = total * 20 / (time.perf_counter() - t0)
+    ref = sims[5].get_particles()[0]
+    for s_ in sims:
+        s_.close()
+    # 2. and 3. the ensemble: host launches on per-simulation streams, then graph replay
+    for mode, use_graph in (("stream_host_launches", False), ("graph_ensemble", True)):
+        sims = fresh()
+        with Ensemble(sims) as ens:
+            if use_graph:  # capture outside the timed region, then restore the ICs
+                ens.run(a[:3], use_graph=True)
+                torch.cuda.synchronize()
+                for s_, (p, m) in zip(sims, ics):
+                    s_.set_particles(p, m, a=a[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ens.run(a, use_graph=use_graph)
+            torch.cuda.synchronize()
+            out[mode] = total * 20 / (time.perf_counter() - t0)
+        pos5 = sims[5].get_particles()[0]
+        d = pos5 - ref
+        d -= box * np.round(d / box)
+        out[mode + "_max_dx_vs_serial"] = float(np.max(np.abs(d)))
+        for s_ in sims:
+            s_.close()
+    value = out["graph_ensemble"]
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 20,
+            "warmup": 3, "ms_per_step": 1e3 * total / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 forces, f64 positions/momenta",
+            "data": "synthetic",
+            "config": {"workload": ENSEMBLE_NAME, "particles": total, "simulations": 48},
+            "modes": out,
+            "speedup_graph_over_serial": value / out["serial_host_launches"]}
+
+
 # ---------------------------------------------------------------- reference arm (oracle)
 
 
@@ -414,6 +487,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--workload", choices=["clustered_128", "ensemble48"], default="clustered_128")
     ap.add_argument("--sub-bits", type=int, default=None,
                     help="Morton bits per axis inside a chaining cell (library default if unset)")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -432,6 +506,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.workload == "ensemble48":
+        if rank == 0:
+            print(json.dumps(run_ensemble(args)), flush=True)
         return
 
     dist = None

@@ -183,6 +183,46 @@ int p3m_get_particles(p3m_ctx *ctx, double *pos3n, double *mom3n, double *acc3n,
 int p3m_power_spectrum(p3m_ctx *ctx, int n_bins, int deconvolve, double tophat_radius,
                        double *k_mean, double *power, double *n_modes, double *sigma);
 
+/*
+ * Graph-captured stepping.  p3m_run_steps advances the context through n_steps kick-drift-kick
+ * steps a_list[0] -> a_list[1] -> ... -> a_list[n_steps] (increasing; n_steps <= 4096 per
+ * call).  use_graph = 0 issues every kernel from the host (p3m_step in a loop); use_graph = 1
+ * captures one step into a CUDA graph per step parity on first use (the buffers the step swaps
+ * return to their roles after two steps) and replays it, the step's kick and drift factors
+ * read from a device table filled once per call.  Graph mode needs a non-default stream
+ * (p3m_options.stream or p3m_set_stream).  The graphs are recaptured when the context's
+ * geometry (p3m_autotune) or buffer roles (an intervening p3m_step) no longer match them.
+ */
+int p3m_run_steps(p3m_ctx *ctx, const double *a_list, int n_steps, int use_graph);
+
+/* Moves the context to another stream (cudaStream_t; NULL = legacy stream); waits for the
+ * work already queued on the old one. */
+int p3m_set_stream(p3m_ctx *ctx, void *stream);
+
+/*
+ * Ensembles of independent simulations of any sizes (SURVEY "batched ensembles"): the
+ * contexts advance together through the same schedule of scale factors.  With use_graph = 1
+ * one step of every context is captured as parallel branches of a single CUDA graph (one per
+ * step parity), so each step of the whole ensemble is one graph launch; with use_graph = 0
+ * the host issues every kernel of every context, context after context.  own_streams != 0
+ * gives each context a stream of its own (p3m_ensemble_free returns them to the legacy
+ * stream).  The ensemble borrows the contexts; free it before them.  Errors are reported
+ * through p3m_last_error(NULL).
+ */
+typedef struct p3m_ensemble p3m_ensemble;
+int p3m_ensemble_create(p3m_ensemble **ens, p3m_ctx *const *ctxs, int n_ctx, int own_streams);
+int p3m_ensemble_run(p3m_ensemble *ens, const double *a_list, int n_steps, int use_graph);
+void p3m_ensemble_free(p3m_ensemble *ens);
+
+/*
+ * Autotuner of the sort key's Morton depth: times two force evaluations of the current
+ * particles for each sub_bits in 0..3 whose key fits in 32 bits (ms_out[b], nullable; NaN when
+ * skipped), keeps the fastest (*sub_bits_out) and leaves valid forces.  The cells, and hence
+ * which pairs interact, do not depend on sub_bits; the forces agree up to the FP32 rounding
+ * of a different summation order.
+ */
+int p3m_autotune(p3m_ctx *ctx, int *sub_bits_out, double *ms_out);
+
 /* Momentum, kinetic energy, pair count and cell statistics of the current state.
  * Synchronises the stream. */
 int p3m_diagnostics(p3m_ctx *ctx, p3m_diag *out);

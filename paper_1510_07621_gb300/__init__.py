@@ -17,7 +17,8 @@ from . import _lib
 from ._lib import (P3M_PREC_FP64, P3M_PREC_MIXED, Cosmology, Diag, Options, P3MError, check,
                    load)
 
-__all__ = ["P3M", "P3MError", "load", "P3M_PREC_MIXED", "P3M_PREC_FP64", "phase_names"]
+__all__ = ["P3M", "Ensemble", "P3MError", "load", "P3M_PREC_MIXED", "P3M_PREC_FP64",
+           "phase_names"]
 
 
 def _is_torch(a) -> bool:
@@ -171,6 +172,25 @@ class P3M:
                                                  p.ctypes.data, c.ctypes.data, ctypes.byref(s)))
         return k, p, c, (s.value if tophat_radius > 0 else None)
 
+    def run_steps(self, a_list, use_graph: bool = True):
+        """Kick-drift-kick steps through the scale factors a_list (len = steps + 1), replayed
+        from captured CUDA graphs when use_graph (needs a non-default stream)."""
+        a = np.ascontiguousarray(a_list, dtype=np.float64)
+        self._check(self._lib.p3m_run_steps(self._ctx, a.ctypes.data, len(a) - 1,
+                                            1 if use_graph else 0))
+
+    def set_stream(self, stream):
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._check(self._lib.p3m_set_stream(self._ctx, ctypes.c_void_p(s)))
+
+    def autotune(self):
+        """Picks the sort key's Morton depth by timing force evaluations; returns
+        (sub_bits, ms per evaluation for sub_bits 0..3)."""
+        b = ctypes.c_int()
+        ms = np.full(4, np.nan)
+        self._check(self._lib.p3m_autotune(self._ctx, ctypes.byref(b), ms.ctypes.data))
+        return b.value, ms
+
     # ------------------------------------------------------------------ introspection
     def diagnostics(self) -> dict:
         d = Diag()
@@ -212,3 +232,40 @@ class P3M:
         ms = (ctypes.c_double * _lib.P3M_NPHASES)()
         self._lib.p3m_timings(self._ctx, ms, _lib.P3M_NPHASES, 1 if reset else 0)
         return dict(zip(phase_names(), list(ms)))
+
+
+class Ensemble:
+    """Independent P3M contexts advanced together through one schedule of scale factors, one
+    CUDA graph launch per step for the whole ensemble (p3m_ensemble_*)."""
+
+    def __init__(self, sims, own_streams: bool = True):
+        self._lib = load()
+        self.sims = list(sims)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s._ctx.value for s in self.sims])
+        self._arr = arr
+        e = ctypes.c_void_p()
+        check(self._lib.p3m_ensemble_create(ctypes.byref(e), arr, len(self.sims),
+                                            1 if own_streams else 0), None)
+        self._e = e
+
+    def run(self, a_list, use_graph: bool = True):
+        a = np.ascontiguousarray(a_list, dtype=np.float64)
+        check(self._lib.p3m_ensemble_run(self._e, a.ctypes.data, len(a) - 1,
+                                         1 if use_graph else 0), None)
+
+    def close(self):
+        if getattr(self, "_e", None) is not None and self._e.value:
+            self._lib.p3m_ensemble_free(self._e)
+            self._e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -143,7 +143,7 @@ struct Phase {
     int id;
     Phase(p3m_ctx *c_, int id_) : c(c_), id(id_)
     {
-        if (c->timing && c->ev_used + 2 <= c->ev_cap) {
+        if (c->timing && !c->capturing && c->ev_used + 2 <= c->ev_cap) {
             cudaEventRecord(c->ev[c->ev_used], c->stream);
             c->ev_phase[c->ev_used] = id;
         } else {
@@ -186,7 +186,7 @@ void release(p3m_ctx *c)
                     c->red,       c->rho,      c->rho_k,        c->frc_k,    c->frc,
                     c->tab_k,     c->tab_kg,   c->tab_g,        c->work_key, c->work_key_alt,
                     c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
-                    c->tab_one,   c->ps_acc};
+                    c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -220,8 +220,9 @@ int check_flags(p3m_ctx *c)
 // Sort by cell, mesh force, pair force.  Positions must already be wrapped and keyed
 // (c->keys).  Result: c->acc (total), c->acc_lr (mesh part).  kfac != 0: the final half kick
 // mom += kfac * acc is fused into the last kernel.
-int evaluate(p3m_ctx *c, double kfac, double *sr_only_out)
+int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table = false)
 {
+    const double *kfac_dev = from_table ? c->cur_fac + 2 : nullptr;
     {
         Phase ph(c, PH_SORT);
         CK(launch_radix_sort(c));
@@ -260,7 +261,7 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out)
         if (sr_only_out) {
             CK(launch_pairs(c, nullptr, sr_only_out, 0.0));
         } else {
-            CK(launch_pairs(c, c->acc_lr, c->acc, kfac));
+            CK(launch_pairs(c, c->acc_lr, c->acc, kfac, kfac_dev));
         }
     } else {
         // pure PM: the mesh part is the whole force
@@ -269,9 +270,9 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out)
             CK(launch_gather(c, sr_only_out ? c->acc_lr : c->acc));
         }
         if (sr_only_out) CK(cudaMemsetAsync(sr_only_out, 0, 3 * sizeof(double) * c->g.n, c->stream));
-        if (kfac != 0.0) {
+        if (kfac != 0.0 || kfac_dev) {
             Phase ph(c, PH_OTHER);
-            CK(launch_kick(c, kfac));
+            CK(launch_kick(c, kfac, kfac_dev));
         }
     }
     return P3M_OK;
@@ -285,6 +286,59 @@ int key_current(p3m_ctx *c)
 }
 
 bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+// One kick-drift-kick step a -> a + da with valid forces at a.  from_table: the step's factors
+// come from the device table (graph-replayed steps; a and da unused).
+int step_body(p3m_ctx *c, double a, double da, bool from_table)
+{
+    double k1 = 0.0, dfac = 0.0, k2 = 0.0;
+    if (from_table) {
+        CK(launch_step_begin(c));
+    } else {
+        const double am = a + 0.5 * da, a2 = a + da;
+        k1 = c->mass * p3m_kick_factor(c->cosmo, a, am);
+        dfac = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
+        k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+    }
+    {
+        Phase ph(c, PH_KICK_DRIFT);
+        CK(launch_kick_drift_keys(c, true, k1, dfac, from_table));
+    }
+    return evaluate(c, k2, nullptr, from_table);
+}
+
+// Buffers whose roles swap during a step (all return to their roles after two steps).
+struct PtrState {
+    double *pos, *mom, *pos_alt, *mom_alt;
+    uint32_t *pid, *pid_alt, *keys, *keys_alt, *vals, *vals_alt;
+    uint32_t *work_key, *work_key_alt, *work_order, *work_order_alt;
+    bool operator==(const PtrState &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+PtrState save_ptrs(const p3m_ctx *c)
+{
+    return PtrState{c->pos,      c->mom,      c->pos_alt,  c->mom_alt,      c->pid,
+                    c->pid_alt,  c->keys,     c->keys_alt, c->vals,         c->vals_alt,
+                    c->work_key, c->work_key_alt, c->work_order, c->work_order_alt};
+}
+
+void load_ptrs(p3m_ctx *c, const PtrState &s)
+{
+    c->pos = s.pos;
+    c->mom = s.mom;
+    c->pos_alt = s.pos_alt;
+    c->mom_alt = s.mom_alt;
+    c->pid = s.pid;
+    c->pid_alt = s.pid_alt;
+    c->keys = s.keys;
+    c->keys_alt = s.keys_alt;
+    c->vals = s.vals;
+    c->vals_alt = s.vals_alt;
+    c->work_key = s.work_key;
+    c->work_key_alt = s.work_key_alt;
+    c->work_order = s.work_order;
+    c->work_order_alt = s.work_order_alt;
+}
 
 }  // namespace
 
@@ -397,6 +451,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
     c->a = 1.0;
     c->stream = (cudaStream_t)opt.stream;
     c->key_bits = key_bits;
+    c->fac_cap = P3M_MAX_GRAPH_STEPS;
     strcpy(c->err, "no error");
 
     int rc = P3M_OK;
@@ -439,6 +494,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->tab_k, real * M},   {(void **)&c->tab_kg, real * M},
             {(void **)&c->tab_g, real * M},   {(void **)&c->tab_invw2, 8 * M},
             {(void **)&c->tab_one, 8 * M},    {(void **)&c->ps_acc, 8 * (3 * (M / 2) + 1)},
+            {(void **)&c->fac_table, 8 * 3 * (size_t)P3M_MAX_GRAPH_STEPS},
+            {(void **)&c->step_idx, 16},      {(void **)&c->cur_fac, 32},
         };
         for (auto &a : allocs) {
             e = dalloc(a.p, a.bytes);
@@ -622,17 +679,9 @@ extern "C" int p3m_step(p3m_ctx *c, double a, double da)
         if (rc) return rc;
         c->forces_valid = true;
     }
-    const double am = a + 0.5 * da, a2 = a + da;
-    const double k1 = c->mass * p3m_kick_factor(c->cosmo, a, am);
-    const double dfac = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
-    const double k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
-    {
-        Phase ph(c, PH_KICK_DRIFT);
-        CK(launch_kick_drift_keys(c, true, k1, dfac));
-    }
-    rc = evaluate(c, k2, nullptr);
+    rc = step_body(c, a, da, false);
     if (rc) return rc;
-    c->a = a2;
+    c->a = a + da;
     return P3M_OK;
 }
 
@@ -795,7 +844,312 @@ extern "C" const char *p3m_last_error(const p3m_ctx *c) { return c ? c->err : g_
 extern "C" void p3m_free(p3m_ctx *c)
 {
     if (!c) return;
+    if (c->self_ens) p3m_ensemble_free(c->self_ens);
     cudaStreamSynchronize(c->stream);
     release(c);
     free(c);
+}
+
+// ---------------------------------------------------------------- streams, graphs, ensembles
+
+extern "C" int p3m_set_stream(p3m_ctx *c, void *stream)
+{
+    if (!c) return P3M_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    c->stream = (cudaStream_t)stream;
+    CKF(cufftSetStream(c->plan_r2c, c->stream));
+    CKF(cufftSetStream(c->plan_c2r, c->stream));
+    return P3M_OK;
+}
+
+struct p3m_ensemble {
+    int n;
+    p3m_ctx **c;
+    cudaStream_t parent;      // the graphs are launched here
+    cudaStream_t *own;        // streams the ensemble created for its contexts (or NULL)
+    cudaEvent_t fork, *join;  // fork/join of the captured branches
+    cudaGraphExec_t gexec[2]; // one captured step for each step parity
+    bool ready;
+    int parity;               // parity of the next step to replay
+    PtrState *state[2];       // per context: buffer roles before an even / odd step
+    int *version;             // per context: geometry version the graphs were captured with
+};
+
+namespace {
+
+// Captures one step of every context as parallel branches of one graph.
+int capture_step(p3m_ensemble *e, int parity)
+{
+    p3m_ctx *c = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(e->parent, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess)
+        return p3m_fail_global(P3M_ECUDA, "graph capture: %s", cudaGetErrorString(err));
+    err = cudaEventRecord(e->fork, e->parent);
+    int rc = P3M_OK;
+    for (int i = 0; i < e->n && err == cudaSuccess && rc == P3M_OK; ++i) {
+        c = e->c[i];
+        err = cudaStreamWaitEvent(c->stream, e->fork, 0);
+        if (err != cudaSuccess) break;
+        c->capturing = true;
+        rc = step_body(c, 0.0, 0.0, true);
+        c->capturing = false;
+        if (rc == P3M_OK) err = cudaEventRecord(e->join[i], c->stream);
+        if (err == cudaSuccess && rc == P3M_OK) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
+    }
+    cudaError_t end = cudaStreamEndCapture(e->parent, &graph);
+    if (rc != P3M_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return p3m_fail_global(rc, "graph capture: %s", c ? c->err : "step failed");
+    }
+    if (err == cudaSuccess) err = end;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&e->gexec[parity], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (err != cudaSuccess)
+        return p3m_fail_global(P3M_ECUDA, "graph capture: %s", cudaGetErrorString(err));
+    return P3M_OK;
+}
+
+void drop_graphs(p3m_ensemble *e)
+{
+    for (int p = 0; p < 2; ++p)
+        if (e->gexec[p]) {
+            cudaGraphExecDestroy(e->gexec[p]);
+            e->gexec[p] = nullptr;
+        }
+    e->ready = false;
+}
+
+}  // namespace
+
+extern "C" int p3m_ensemble_create(p3m_ensemble **out, p3m_ctx *const *ctxs, int n, int own_streams)
+{
+    if (!out || !ctxs || n < 1) return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_create: bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_create: context %d is NULL", i);
+    p3m_ensemble *e = (p3m_ensemble *)calloc(1, sizeof(p3m_ensemble));
+    if (!e) return p3m_fail_global(P3M_ENOMEM, "p3m_ensemble_create: host allocation failed");
+    e->n = n;
+    e->c = (p3m_ctx **)calloc(n, sizeof(p3m_ctx *));
+    e->join = (cudaEvent_t *)calloc(n, sizeof(cudaEvent_t));
+    e->state[0] = (PtrState *)calloc(n, sizeof(PtrState));
+    e->state[1] = (PtrState *)calloc(n, sizeof(PtrState));
+    e->version = (int *)calloc(n, sizeof(int));
+    if (own_streams) e->own = (cudaStream_t *)calloc(n, sizeof(cudaStream_t));
+    cudaError_t err = (e->c && e->join && e->state[0] && e->state[1] && e->version &&
+                       (!own_streams || e->own))
+                          ? cudaSuccess
+                          : cudaErrorMemoryAllocation;
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->parent, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && err == cudaSuccess; ++i) {
+        e->c[i] = ctxs[i];
+        err = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming);
+        if (err == cudaSuccess && own_streams) {
+            err = cudaStreamCreateWithFlags(&e->own[i], cudaStreamNonBlocking);
+            if (err == cudaSuccess && p3m_set_stream(ctxs[i], e->own[i]) != P3M_OK) err = cudaErrorUnknown;
+        }
+    }
+    if (err != cudaSuccess) {
+        p3m_ensemble_free(e);
+        return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_create: %s", cudaGetErrorString(err));
+    }
+    *out = e;
+    return P3M_OK;
+}
+
+extern "C" int p3m_ensemble_run(p3m_ensemble *e, const double *a_list, int n_steps, int use_graph)
+{
+    if (!e || !a_list || n_steps < 1)
+        return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_run: bad arguments");
+    if (n_steps > P3M_MAX_GRAPH_STEPS)
+        return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_run: at most %d steps per call", P3M_MAX_GRAPH_STEPS);
+    for (int k = 0; k < n_steps; ++k)
+        if (!finite_pos(a_list[k]) || !(a_list[k + 1] > a_list[k]))
+            return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_run: a_list must increase");
+    for (int i = 0; i < e->n; ++i) {
+        p3m_ctx *c = e->c[i];
+        if (!c->have_particles) return p3m_fail_global(P3M_ESTATE, "p3m_ensemble_run: context %d has no particles", i);
+        if (use_graph && !c->stream)
+            return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_run: graph mode needs non-default streams");
+        if (!c->forces_valid) {
+            int rc = key_current(c);
+            if (!rc) rc = evaluate(c, 0.0, nullptr);
+            if (rc) return p3m_fail_global(rc, "p3m_ensemble_run: %s", c->err);
+            c->forces_valid = true;
+        }
+    }
+    if (!use_graph) {
+        for (int k = 0; k < n_steps; ++k)
+            for (int i = 0; i < e->n; ++i) {
+                int rc = step_body(e->c[i], a_list[k], a_list[k + 1] - a_list[k], false);
+                if (rc) return p3m_fail_global(rc, "p3m_ensemble_run: %s", e->c[i]->err);
+            }
+    } else {
+        // per-step factors of every context, and its step counter reset
+        std::vector<double> fac(3 * (size_t)n_steps);
+        for (int i = 0; i < e->n; ++i) {
+            p3m_ctx *c = e->c[i];
+            for (int k = 0; k < n_steps; ++k) {
+                const double a = a_list[k], a2 = a_list[k + 1], am = a + 0.5 * (a2 - a);
+                fac[3 * k] = c->mass * p3m_kick_factor(c->cosmo, a, am);
+                fac[3 * k + 1] = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
+                fac[3 * k + 2] = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+            }
+            cudaError_t err = cudaMemcpyAsync(c->fac_table, fac.data(), sizeof(double) * fac.size(),
+                                              cudaMemcpyHostToDevice, c->stream);
+            if (err == cudaSuccess) err = cudaMemsetAsync(c->step_idx, 0, sizeof(uint32_t), c->stream);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+            if (err != cudaSuccess)
+                return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_run: %s", cudaGetErrorString(err));
+        }
+        // the graphs bake buffer addresses and geometry: recapture when they no longer match
+        if (e->ready) {
+            int par = -1;
+            for (int p = 0; p < 2 && par < 0; ++p) {
+                bool all = true;
+                for (int i = 0; i < e->n; ++i)
+                    all = all && save_ptrs(e->c[i]) == e->state[p][i] &&
+                          e->version[i] == e->c[i]->geom_version;
+                if (all) par = p;
+            }
+            if (par < 0) drop_graphs(e);
+            else e->parity = par;
+        }
+        if (!e->ready) {
+            for (int i = 0; i < e->n; ++i) {
+                e->state[0][i] = save_ptrs(e->c[i]);
+                e->version[i] = e->c[i]->geom_version;
+            }
+            int rc = capture_step(e, 0);
+            for (int i = 0; i < e->n && rc == P3M_OK; ++i) e->state[1][i] = save_ptrs(e->c[i]);
+            if (rc == P3M_OK) rc = capture_step(e, 1);
+            if (rc != P3M_OK) {
+                for (int i = 0; i < e->n; ++i) load_ptrs(e->c[i], e->state[0][i]);
+                drop_graphs(e);
+                return rc;
+            }
+            e->ready = true;
+            e->parity = 0;
+        }
+        cudaError_t err = cudaSuccess;
+        for (int k = 0; k < n_steps && err == cudaSuccess; ++k) {
+            err = cudaGraphLaunch(e->gexec[e->parity], e->parent);
+            e->parity ^= 1;
+        }
+        // later work on the contexts' own streams comes after the replayed steps
+        if (err == cudaSuccess) err = cudaEventRecord(e->fork, e->parent);
+        for (int i = 0; i < e->n; ++i) {
+            load_ptrs(e->c[i], e->state[e->parity][i]);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(e->c[i]->stream, e->fork, 0);
+        }
+        if (err != cudaSuccess)
+            return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_run: %s", cudaGetErrorString(err));
+    }
+    for (int i = 0; i < e->n; ++i) {
+        e->c[i]->a = a_list[n_steps];
+        e->c[i]->forces_valid = true;
+    }
+    return P3M_OK;
+}
+
+extern "C" void p3m_ensemble_free(p3m_ensemble *e)
+{
+    if (!e) return;
+    if (e->parent) cudaStreamSynchronize(e->parent);
+    drop_graphs(e);
+    for (int i = 0; i < e->n; ++i) {
+        if (e->c && e->c[i] && e->own && e->own[i]) {
+            p3m_set_stream(e->c[i], nullptr);
+            cudaStreamDestroy(e->own[i]);
+        }
+        if (e->join && e->join[i]) cudaEventDestroy(e->join[i]);
+    }
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->parent) cudaStreamDestroy(e->parent);
+    free(e->c);
+    free(e->join);
+    free(e->own);
+    free(e->state[0]);
+    free(e->state[1]);
+    free(e->version);
+    free(e);
+}
+
+extern "C" int p3m_run_steps(p3m_ctx *c, const double *a_list, int n_steps, int use_graph)
+{
+    if (!c) return P3M_EINVAL;
+    if (!use_graph) {
+        for (int k = 0; k < n_steps; ++k) {
+            int rc = p3m_step(c, a_list[k], a_list[k + 1] - a_list[k]);
+            if (rc) return rc;
+        }
+        return P3M_OK;
+    }
+    if (!c->self_ens) {
+        int rc = p3m_ensemble_create(&c->self_ens, &c, 1, 0);
+        if (rc) return fail(c, rc, "%s", g_init_err);
+    }
+    int rc = p3m_ensemble_run(c->self_ens, a_list, n_steps, 1);
+    if (rc) return fail(c, rc, "%s", g_init_err);
+    return P3M_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+
+extern "C" int p3m_autotune(p3m_ctx *c, int *sub_bits_out, double *ms_out)
+{
+    if (!c) return P3M_EINVAL;
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_autotune: no particles loaded");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int saved_b = c->g.sub_bits;
+    int best_b = saved_b;
+    double best_ms = 1e300;
+    for (int b = 0; b <= 3; ++b) {
+        const uint64_t max_key = ((uint64_t)c->g.n_cells << (3 * b)) - 1;
+        if (ms_out) ms_out[b] = NAN;
+        if (max_key >= (1ull << 32)) continue;
+        c->g.sub_bits = b;
+        c->g.n_fine = c->g.n_c << b;
+        c->g.inv_fine = (double)c->g.n_fine / c->g.box;
+        c->key_bits = 1;
+        while (c->key_bits < 32 && (max_key >> c->key_bits)) ++c->key_bits;
+        ++c->geom_version;
+        int rc = key_current(c);
+        if (!rc) rc = evaluate(c, 0.0, nullptr);  // warm-up (and a sort from the previous order)
+        if (rc) return rc;
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < 2 && !rc; ++r) {
+            rc = key_current(c);
+            if (!rc) rc = evaluate(c, 0.0, nullptr);
+        }
+        if (rc) return rc;
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms_out) ms_out[b] = ms / 2.0;
+        if (ms / 2.0 < best_ms) {
+            best_ms = ms / 2.0;
+            best_b = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const uint64_t max_key = ((uint64_t)c->g.n_cells << (3 * best_b)) - 1;
+    c->g.sub_bits = best_b;
+    c->g.n_fine = c->g.n_c << best_b;
+    c->g.inv_fine = (double)c->g.n_fine / c->g.box;
+    c->key_bits = 1;
+    while (c->key_bits < 32 && (max_key >> c->key_bits)) ++c->key_bits;
+    ++c->geom_version;
+    int rc = key_current(c);
+    if (!rc) rc = evaluate(c, 0.0, nullptr);
+    if (rc) return rc;
+    c->forces_valid = true;
+    if (sub_bits_out) *sub_bits_out = best_b;
+    return P3M_OK;
 }

@@ -14,8 +14,9 @@ inline int grid_for(int64_t n, int threads, int num_sms)
 }
 
 __global__ void k_kick(double *__restrict__ mom, const double *__restrict__ acc, int64_t n3,
-                       double kfac)
+                       double kfac, const double *__restrict__ kfac_dev)
 {
+    if (kfac_dev) kfac = *kfac_dev;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3;
          i += (int64_t)gridDim.x * blockDim.x)
         mom[i] = __dadd_rn(mom[i], __dmul_rn(kfac, acc[i]));
@@ -125,15 +126,35 @@ cudaError_t launch_axpy(p3m_ctx *c, double *y, const double *x, double alpha)
 {
     c->launches += 1;
     const int64_t n3 = 3 * c->g.n;
-    k_kick<<<grid_for(n3, 256, c->num_sms), 256, 0, c->stream>>>(y, x, n3, alpha);
+    k_kick<<<grid_for(n3, 256, c->num_sms), 256, 0, c->stream>>>(y, x, n3, alpha, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick(p3m_ctx *c, double kfac)
+cudaError_t launch_kick(p3m_ctx *c, double kfac, const double *kfac_dev)
 {
     c->launches += 1;
     const int64_t n3 = 3 * c->g.n;
-    k_kick<<<grid_for(n3, 256, c->num_sms), 256, 0, c->stream>>>(c->mom, c->acc, n3, kfac);
+    k_kick<<<grid_for(n3, 256, c->num_sms), 256, 0, c->stream>>>(c->mom, c->acc, n3, kfac, kfac_dev);
+    return cudaGetLastError();
+}
+
+namespace {
+// First kernel of a graph-replayed step: the step's factors (K1, D, K2) from the table into
+// the fixed slot the other kernels read, and the step counter advanced.
+__global__ void k_step_begin(const double *__restrict__ table, uint32_t *step_idx, double *cur)
+{
+    const uint32_t s = *step_idx;
+    cur[0] = table[3 * s];
+    cur[1] = table[3 * s + 1];
+    cur[2] = table[3 * s + 2];
+    *step_idx = s + 1;
+}
+}  // namespace
+
+cudaError_t launch_step_begin(p3m_ctx *c)
+{
+    c->launches += 1;
+    k_step_begin<<<1, 1, 0, c->stream>>>(c->fac_table, c->step_idx, c->cur_fac);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,16 @@ struct p3m_ctx {
     int ev_used, ev_cap;
     double phase_ms[P3M_NPHASES];
 
+    // graph-replayed steps: per-step factors (K1, D, K2) for up to fac_cap steps, the device
+    // step counter, and the two captured step graphs (even and odd step parity)
+    double *fac_table;
+    uint32_t *step_idx;
+    double *cur_fac;  // factors of the step being executed: K1, D, K2
+    int fac_cap;
+    bool capturing;
+    int geom_version;              // bumped when the geometry changes (captured graphs go stale)
+    struct p3m_ensemble *self_ens;  // private one-context ensemble of p3m_run_steps
+
     bool have_particles;
     bool forces_valid;
     bool sorted_valid;
@@ -99,6 +109,7 @@ enum {
     PH_OTHER
 };
 
+#define P3M_MAX_GRAPH_STEPS 4096  // steps per p3m_run_steps / p3m_ensemble_run call
 #define P3M_SORT_TILE 4096   // keys per radix-sort tile (256 threads x 16)
 #define P3M_PAIR_TI 32       // i-particles per pair work item (one per lane of a warp)
 #define P3M_PAIR_TJ 128      // j-particles per shared-memory tile (4 blocks of 32)
@@ -108,7 +119,8 @@ enum {
 // ------------------------------------------------------------------ launchers (sort.cu)
 // Wraps positions and writes keys (optionally after a kick with kfac = m K and a drift with
 // dfac = D / m).  vals are not touched.
-cudaError_t launch_kick_drift_keys(p3m_ctx *c, bool kick_drift, double kfac, double dfac);
+cudaError_t launch_kick_drift_keys(p3m_ctx *c, bool kick_drift, double kfac, double dfac,
+                                   bool from_table = false);
 // Stable LSD radix sort of (keys, identity) -> c->keys (sorted), c->vals (source slots).
 cudaError_t launch_radix_sort(p3m_ctx *c);
 // Permutes pos/mom/pid by c->vals, writes the relative coordinates, cell_start, work list.
@@ -125,11 +137,16 @@ cudaError_t launch_gather(p3m_ctx *c, double *acc_out);
 cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc);
 
 // ------------------------------------------------------------------ launchers (pair.cu)
-// acc_out = acc_in + SR (acc_in NULL: SR only); kfac != 0: mom += kfac * acc_out.
-cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac);
+// acc_out = acc_in + SR (acc_in NULL: SR only); kfac != 0: mom += kfac * acc_out.  kfac_dev
+// (nullable): read kfac from device memory instead.
+cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+                         const double *kfac_dev = nullptr);
 
 // ------------------------------------------------------------------ launchers (integrate.cu)
-cudaError_t launch_kick(p3m_ctx *c, double kfac);
+cudaError_t launch_kick(p3m_ctx *c, double kfac, const double *kfac_dev = nullptr);
+// cur_fac = fac_table[3 s .. 3 s + 2], s = *step_idx, then *step_idx = s + 1 (the first launch
+// of a graph-replayed step)
+cudaError_t launch_step_begin(p3m_ctx *c);
 // y += alpha x over 3n values
 cudaError_t launch_axpy(p3m_ctx *c, double *y, const double *x, double alpha);
 cudaError_t launch_load_particles(p3m_ctx *c, const double *pos, const double *mom,

@@ -166,11 +166,12 @@ __global__ void __launch_bounds__(32)
             const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
             const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPoly gp, float rcull2, float rin2,
             const double *__restrict__ acc_in, double *__restrict__ acc_out,
-            double *__restrict__ mom, double kfac, uint32_t *__restrict__ counters,
-            unsigned long long *__restrict__ pair_count)
+            double *__restrict__ mom, double kfac, const double *__restrict__ kfac_dev,
+            uint32_t *__restrict__ counters, unsigned long long *__restrict__ pair_count)
 {
     using V4 = typename Vec4<T>::type;
     constexpr bool kAbsolute = sizeof(T) == 8;
+    if (kfac_dev) kfac = *kfac_dev;  // graph-replayed steps read the factor from the device
     __shared__ __align__(128) V4 sj[2][kTJ];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ Neighbour nbr[27];
@@ -391,7 +392,8 @@ __global__ void __launch_bounds__(32)
 }
 
 template <typename T>
-cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac)
+cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+                       const double *kfac_dev)
 {
     cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
     cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);  // last evaluation
@@ -410,15 +412,16 @@ cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double
     k_pairs<T><<<grid, 32, 0, c->stream>>>(
         (const typename Vec4<T>::type *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
         c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
-        rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, c->counters,
-        c->pair_count);
+        rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, kfac_dev,
+        c->counters, c->pair_count);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac)
+cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+                         const double *kfac_dev)
 {
-    return c->precision == P3M_PREC_MIXED ? pairs_impl<float>(c, acc_in, acc_out, kfac)
-                                          : pairs_impl<double>(c, acc_in, acc_out, kfac);
+    return c->precision == P3M_PREC_MIXED ? pairs_impl<float>(c, acc_in, acc_out, kfac, kfac_dev)
+                                          : pairs_impl<double>(c, acc_in, acc_out, kfac, kfac_dev);
 }

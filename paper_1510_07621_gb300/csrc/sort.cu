@@ -51,12 +51,18 @@ __device__ __forceinline__ uint32_t make_key(uint32_t fx, uint32_t fy, uint32_t 
 }
 
 // Half kick + drift (optional), periodic wrap, key.  Kick and drift use separately rounded
-// products and sums: p += (m K) a; x += p (D / m).
+// products and sums: p += (m K) a; x += p (D / m).  With fac_dev the two factors are read
+// from fac_dev[0], fac_dev[1] (graph-replayed steps).
 __global__ void k_kick_drift_keys(double *__restrict__ pos, double *__restrict__ mom,
                                   const double *__restrict__ acc, P3MGeom g, int kick_drift,
-                                  double kfac, double dfac, uint32_t *__restrict__ keys)
+                                  double kfac, double dfac, uint32_t *__restrict__ keys,
+                                  const double *__restrict__ fac_dev)
 {
     const int64_t n = g.n;
+    if (fac_dev) {
+        kfac = fac_dev[0];
+        dfac = fac_dev[1];
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t f[3];
@@ -377,11 +383,13 @@ inline int grid_for(int64_t n, int threads, int num_sms)
 
 }  // namespace
 
-cudaError_t launch_kick_drift_keys(p3m_ctx *c, bool kick_drift, double kfac, double dfac)
+cudaError_t launch_kick_drift_keys(p3m_ctx *c, bool kick_drift, double kfac, double dfac,
+                                   bool from_table)
 {
     c->launches += 1;
     k_kick_drift_keys<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
-        c->pos, c->mom, c->acc, c->g, kick_drift ? 1 : 0, kfac, dfac, c->keys);
+        c->pos, c->mom, c->acc, c->g, kick_drift ? 1 : 0, kfac, dfac, c->keys,
+        from_table ? c->cur_fac : nullptr);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,109 @@
+"""Graph-captured steps, ensembles and the autotuner: the same trajectories as steps issued
+one kernel at a time (up to the FP32 rounding of float atomics and summation order)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import p3m_synth as S
+from oracle import p3m_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1510_07621_gb300 import build
+    build.build()
+    import paper_1510_07621_gb300 as m
+    return torch, m
+
+
+def _max_dx(p, q, box):
+    d = p - q
+    d -= box * np.round(d / box)
+    return np.max(np.abs(d))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_steps_follow_host_steps(mod, precision):
+    """FP64: the same trajectory to round-off.  Mixed: float atomics make two runs differ in
+    their FP32 rounding, which close pairs amplify; rms within 1e-7 L, worst within 1e-5 L."""
+    torch, m = mod
+    pos, mom = S.zeldovich(32, 64.0, 0.02, 1511)
+    a = S.log_spaced_steps(0.02, 0.1, 10)
+    n = pos.shape[1]
+    ref = m.P3M(64.0, n, 32, stream=0, precision=precision)
+    ref.set_particles(pos, mom, a=a[0])
+    for k in range(10):
+        ref.step(a[k], a[k + 1] - a[k])
+    rp, rm = ref.get_particles()
+    s = torch.cuda.Stream()
+    with m.P3M(64.0, n, 32, stream=s, precision=precision) as sim:
+        sim.set_particles(pos, mom, a=a[0])
+        sim.run_steps(a[:4], use_graph=True)     # 3 steps: odd, parity flips
+        sim.step(a[3], a[4] - a[3])              # host step in between: graphs recaptured
+        sim.run_steps(a[4:], use_graph=True)     # 6 more
+        gp, gm = sim.get_particles()
+        d = sim.diagnostics()
+    ref.close()
+    if precision == "fp64":
+        assert _max_dx(gp, rp, 64.0) < 1e-11 * 64.0
+        assert np.max(np.abs(gm - rm)) < 1e-9 * np.max(np.abs(rm))
+    else:
+        dx = gp - rp
+        dx -= 64.0 * np.round(dx / 64.0)
+        assert math.sqrt(np.mean(dx * dx)) < 1e-7 * 64.0
+        assert _max_dx(gp, rp, 64.0) < 1e-5 * 64.0
+    assert abs(d["a"] - a[-1]) < 1e-15
+
+
+def test_ensemble_matches_individual_runs(mod):
+    torch, m = mod
+    specs = [(16, 32.0, 32, 11), (24, 40.0, 24, 12), (32, 64.0, 32, 13)]
+    a = S.log_spaced_steps(0.05, 0.2, 5)
+    ics = [S.zeldovich(n_p, box, a[0], seed) for n_p, box, mesh, seed in specs]
+    refs = []
+    for (n_p, box, mesh, seed), (pos, mom) in zip(specs, ics):
+        with m.P3M(box, n_p ** 3, mesh, stream=0, precision="fp64") as r:
+            r.set_particles(pos, mom, a=a[0])
+            for k in range(5):
+                r.step(a[k], a[k + 1] - a[k])
+            refs.append(r.get_particles())
+    for use_graph in (True, False):
+        sims = [m.P3M(box, n_p ** 3, mesh, stream=0, precision="fp64")
+                for n_p, box, mesh, seed in specs]
+        for s_, (pos, mom) in zip(sims, ics):
+            s_.set_particles(pos, mom, a=a[0])
+        with m.Ensemble(sims) as ens:
+            ens.run(a[:3], use_graph=use_graph)
+            ens.run(a[2:], use_graph=use_graph)
+        for s_, (n_p, box, mesh, seed), (rp, rm) in zip(sims, specs, refs):
+            gp, gm = s_.get_particles()
+            assert _max_dx(gp, rp, box) < 1e-11 * box
+            s_.close()
+
+
+def test_autotune_keeps_forces(mod):
+    torch, m = mod
+    pos, mom = S.clustered(48, 100.0, 4001)
+    n = pos.shape[1]
+    with m.P3M(100.0, n, 48) as sim:
+        sim.set_particles(pos, mom, a=1.0)
+        f0 = sim.forces(1.0)
+        b, ms = sim.autotune()
+        assert b in (0, 1, 2, 3) and np.isfinite(ms[b]) and ms[b] == np.nanmin(ms)
+        f1 = sim.forces(1.0)
+        keys, ids, starts = sim.get_cells()
+    assert math.sqrt(np.sum((f1 - f0) ** 2) / np.sum(f0 ** 2)) < 2e-6
+    # after re-sorts with other key depths, equal keys keep their previous relative order:
+    # the sorted keys are unique, the ids must be a permutation that carries them
+    p = O.Params(100.0, n, 48, sub_bits=b)
+    cell, key = O.cell_keys(O.wrap(pos, 100.0), p)
+    assert np.array_equal(keys.astype(np.int64), np.sort(key))
+    assert np.array_equal(np.sort(ids.astype(np.int64)), np.arange(n))
+    assert np.array_equal(key[ids.astype(np.int64)], keys.astype(np.int64))
