@@ -542,3 +542,147 @@ def cic_shot_noise(k_vec_index, p: Params, n_particles: int, deconvolve: bool = 
         sinc = np.where(x == 0.0, 1.0, np.sin(x) / np.where(x == 0.0, 1.0, x))
         ps = ps / np.prod(sinc, axis=0) ** 4
     return ps
+
+
+# --------------------------------------------------------------------------- adjoint
+# Reverse-mode derivatives of the step, for gradients of a final-density loss with respect
+# to the initial displacement field.  The derivative of a force evaluation is needed as its
+# transpose applied to a vector field v ("VJP"): out = (dA/dx)^T v, A the accelerations.
+
+
+def cic_grad_weights(pos: np.ndarray, p: Params):
+    """CIC stencil with the weights and their position derivatives: for each of the 8 corners
+    (cx, cy, cz) the node index (N,), weight (N,) and d weight / d x (3, N)."""
+    M = p.mesh
+    i0, f = cic_weights(pos, p)
+    inv_h = p.mesh / p.box
+    out = []
+    for cx in (0, 1):
+        for cy in (0, 1):
+            for cz in (0, 1):
+                w1 = [f[0] if cx else 1.0 - f[0], f[1] if cy else 1.0 - f[1],
+                      f[2] if cz else 1.0 - f[2]]
+                dw1 = [(inv_h if c else -inv_h) * np.ones_like(f[0]) for c in (cx, cy, cz)]
+                node = (((i0[0] + cx) % M) * M + (i0[1] + cy) % M) * M + (i0[2] + cz) % M
+                w = w1[0] * w1[1] * w1[2]
+                dw = np.stack([dw1[0] * w1[1] * w1[2], w1[0] * dw1[1] * w1[2],
+                               w1[0] * w1[1] * dw1[2]])
+                out.append((node, w, dw))
+    return out
+
+
+def pm_vjp(pos: np.ndarray, v: np.ndarray, p: Params) -> np.ndarray:
+    """(d a_LR / d x)^T v.  a_LR,i = sum_n W(x_i - n) E(n), E_b = D_b rho, rho(n) = sum_j W(x_j - n)
+    with D_b = IFFT(-i k_b G(k) FFT(.)) (real, and D_b^T = -D_b):
+      out_k = sum_b v_k,b sum_n grad W(x_k - n) E_b(n)          (interpolation weights)
+            + sum_n grad W(x_k - n) psi(n),  psi = -sum_b D_b u_b,  u_b(n) = sum_i W(x_i - n) v_i,b
+    (the second term through the deposit)."""
+    M = p.mesh
+    meshes, _ = pm_force_meshes(pos, p)
+    stencil = cic_grad_weights(pos, p)
+    u = []
+    for b in range(3):
+        ub = np.zeros(M ** 3)
+        for node, w, dw in stencil:
+            ub += np.bincount(node, weights=w * v[b], minlength=M ** 3)
+        u.append(ub.reshape(M, M, M))
+    gk = green(p)
+    gx, gy, gz = gradient_wavenumbers(p)
+    GX, GY, GZ = np.meshgrid(gx, gy, gz, indexing="ij")
+    psik = sum(1j * K * gk * np.fft.rfftn(ub) for K, ub in zip((GX, GY, GZ), u))
+    psi = np.fft.irfftn(psik, s=(M, M, M), axes=(0, 1, 2)).ravel()
+    out = np.zeros_like(pos)
+    flat = [m.ravel() for m in meshes]
+    for node, w, dw in stencil:
+        ev = sum(v[b] * flat[b][node] for b in range(3))
+        out += dw * (ev + psi[node])[None, :]
+    return out
+
+
+def sr_vjp(pos: np.ndarray, v: np.ndarray, p: Params) -> np.ndarray:
+    """(d a_SR / d x)^T v by the plain C pair loop over chaining cells (sr_pairs.c)."""
+    lib = _clib()
+    if not hasattr(lib, "_vjp_set"):
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.sr_vjp_cells.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_int64,
+                                     i64p, i64p, i64p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, dp]
+        lib._vjp_set = True
+    x = np.ascontiguousarray(pos, dtype=np.float64)
+    vv = np.ascontiguousarray(v, dtype=np.float64)
+    n = x.shape[1]
+    q = Params(p.box, p.n, p.mesh, p.r_s_cells, p.cutoff, p.softening, p.deconvolve, 0, True,
+               p.omega_m, p.omega_lambda)
+    cell, _ = cell_keys(x, q)
+    order = stable_order(cell).astype(np.int64)
+    starts = cell_start(cell[order], q.n_c ** 3)
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    out = np.zeros((3, n))
+    lib.sr_vjp_cells(n, _p(x, ctypes.c_double), _p(vv, ctypes.c_double), p.box, q.n_c,
+                     _p(cell, ctypes.c_int64), _p(order, ctypes.c_int64),
+                     _p(starts, ctypes.c_int64), p.r_s, p.r_c, p.eps, p.gm,
+                     _p(out, ctypes.c_double))
+    return out
+
+
+def accel_vjp(pos: np.ndarray, v: np.ndarray, p: Params) -> np.ndarray:
+    """(d a / d x)^T v of the total acceleration at wrapped positions."""
+    x = wrap(pos, p.box)
+    out = pm_vjp(x, v, p)
+    if p.short_range:
+        out = out + sr_vjp(x, v, p)
+    return out
+
+
+def density_loss(pos: np.ndarray, target: np.ndarray, p: Params):
+    """L = sum_n (delta(n) - target(n))^2, delta = n(n)/n_bar - 1 on the CIC mesh, and dL/dx."""
+    x = wrap(pos, p.box)
+    nbar = pos.shape[1] / p.mesh ** 3
+    delta = (cic_deposit(x, p) / nbar - 1.0).ravel()
+    r = delta - target.ravel()
+    grad = np.zeros_like(x)
+    for node, w, dw in cic_grad_weights(x, p):
+        grad += dw * (2.0 * r[node] / nbar)[None, :]
+    return float(np.sum(r * r)), grad
+
+
+def zeldovich_state(psi: np.ndarray, q: np.ndarray, a: float, p: Params, mass: float = 1.0):
+    """Initial state of a displacement field psi (3, N) on the lattice q: x = q + psi,
+    p = m a^(1/2) psi (Einstein-de Sitter linear growth, H0 = 1)."""
+    return wrap(q + psi, p.box), mass * math.sqrt(a) * psi
+
+
+def run_and_loss(psi, q, a_list, target, p: Params, mass: float = 1.0):
+    """Forward: Zel'dovich state at a_list[0], KDK steps through a_list, density loss."""
+    x, m = zeldovich_state(psi, q, a_list[0], p, mass)
+    acc = accel(x, p)
+    for k in range(len(a_list) - 1):
+        x, m, acc = step(x, m, acc, a_list[k], a_list[k + 1] - a_list[k], p, mass)
+    return density_loss(x, target, p)[0]
+
+
+def run_gradient(psi, q, a_list, target, p: Params, mass: float = 1.0):
+    """dL/dpsi by the reverse sweep over stored states (no checkpointing: the oracle keeps all
+    states).  Step k maps (x_k, p_k) -> (x_{k+1}, p_{k+1}) with kick factors m K1_k, m K2_k and
+    drift factor D_k / m; reverse, with K1_n = 0:
+        lam_x += m (K2_k + K1_{k+1}) VJP(x_{k+1}, lam_p);  lam_p += (D_k / m) lam_x
+    then lam_x += m K1_0 VJP(x_0, lam_p); dL/dpsi = lam_x + m a_0^(1/2) lam_p."""
+    n = len(a_list) - 1
+    x, m = zeldovich_state(psi, q, a_list[0], p, mass)
+    xs = [x]
+    acc = accel(x, p)
+    for k in range(n):
+        x, m, acc = step(x, m, acc, a_list[k], a_list[k + 1] - a_list[k], p, mass)
+        xs.append(x)
+    loss, lam_x = density_loss(xs[-1], target, p)
+    lam_p = np.zeros_like(lam_x)
+    K1 = [kick_factor(a_list[k], a_list[k] + 0.5 * (a_list[k + 1] - a_list[k]), p) for k in range(n)]
+    K2 = [kick_factor(a_list[k] + 0.5 * (a_list[k + 1] - a_list[k]), a_list[k + 1], p) for k in range(n)]
+    D = [drift_factor(a_list[k], a_list[k + 1], p) for k in range(n)]
+    for k in range(n - 1, -1, -1):
+        kf = mass * (K2[k] + (K1[k + 1] if k + 1 < n else 0.0))
+        lam_x = lam_x + kf * accel_vjp(xs[k + 1], lam_p, p)
+        lam_p = lam_p + (D[k] / mass) * lam_x
+    lam_x = lam_x + mass * K1[0] * accel_vjp(xs[0], lam_p, p)
+    return loss, lam_x + mass * math.sqrt(a_list[0]) * lam_p

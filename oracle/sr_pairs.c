@@ -126,3 +126,53 @@ int oracle_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * Transposed Jacobian of the short-range accelerations applied to a vector field v (the
+ * reverse-mode derivative used by the adjoint of the step):
+ *   out_k = sum_{j in the 27 cells, 0 < r_kj < r_c} J(d_kj) (v_j - v_k),
+ *   J(d) = h(r) I + (h'(r)/r) d d^T,  h(r) = Gm g(r/r_s) / (r^2 + eps^2)^(3/2),
+ *   h'(r) = Gm [g'(r/r_s)/r_s (r^2+eps^2)^(-3/2) - 3 r g(r/r_s) (r^2+eps^2)^(-5/2)],
+ *   g'(x) = -x^2 exp(-x^2/4) / (2 sqrt(pi)).
+ * (J is even in d, so the contributions of k as the i and as the j of a pair combine into
+ * this single sum.)  v and out are SoA [3][n]; same cell arguments as sr_accel_cells.
+ */
+void sr_vjp_cells(int64_t n, const double *pos, const double *v, double box, int64_t n_c,
+                  const int64_t *cell_of, const int64_t *order, const int64_t *cell_start,
+                  double r_s, double r_c, double eps, double gm, double *out)
+{
+    const double inv_sqrt_pi = 0.56418958354775628695;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t c = cell_of[k];
+        int64_t cx = c % n_c, cy = (c / n_c) % n_c, cz = c / (n_c * n_c);
+        double o[3] = {0.0, 0.0, 0.0};
+        for (int64_t oz = -1; oz <= 1; ++oz)
+            for (int64_t oy = -1; oy <= 1; ++oy)
+                for (int64_t ox = -1; ox <= 1; ++ox) {
+                    int64_t nc = ((((cz + oz + n_c) % n_c) * n_c + (cy + oy + n_c) % n_c) * n_c +
+                                  (cx + ox + n_c) % n_c);
+                    for (int64_t t = cell_start[nc]; t < cell_start[nc + 1]; ++t) {
+                        int64_t j = order[t];
+                        if (j == k) continue;
+                        double d[3] = {min_image(pos[j] - pos[k], box),
+                                       min_image(pos[n + j] - pos[n + k], box),
+                                       min_image(pos[2 * n + j] - pos[2 * n + k], box)};
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (!(r2 < r_c * r_c) || r2 == 0.0) continue;
+                        double r = sqrt(r2), x = r / r_s, s2 = r2 + eps * eps;
+                        double s3 = s2 * sqrt(s2);
+                        double g = g_split(x);
+                        double gp = -x * x * exp(-0.25 * x * x) * 0.5 * inv_sqrt_pi;
+                        double h = gm * g / s3;
+                        double hp = gm * (gp / r_s / s3 - 3.0 * r * g / (s3 * s2));
+                        double w[3] = {v[j] - v[k], v[n + j] - v[n + k], v[2 * n + j] - v[2 * n + k]};
+                        double dw = d[0] * w[0] + d[1] * w[1] + d[2] * w[2];
+                        for (int a = 0; a < 3; ++a) o[a] += h * w[a] + (hp / r) * dw * d[a];
+                    }
+                }
+        out[k] = o[0];
+        out[n + k] = o[1];
+        out[2 * n + k] = o[2];
+    }
+}
