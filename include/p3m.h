@@ -223,6 +223,32 @@ void p3m_ensemble_free(p3m_ensemble *ens);
  */
 int p3m_autotune(p3m_ctx *ctx, int *sub_bits_out, double *ms_out);
 
+/*
+ * Reverse-mode derivatives, for gradients through the step (SURVEY "differentiable P3M"):
+ *
+ * p3m_force_vjp: out3n = (dA/dx)^T v3n, the transposed Jacobian of the accelerations A at the
+ *   current positions applied to the vector field v [3][n] (caller order).  The mesh part is
+ *   the CIC gather/deposit transposed through the conjugate Green's-function multiply; the
+ *   pair part is sum_j J(d_kj)(v_j - v_k) with J the 3x3 Jacobian of the pair force.  Sorts
+ *   and evaluates the mesh part at the current positions (cached forces are invalidated with
+ *   P3M: the next p3m_step re-evaluates them).  The discontinuities of the
+ *   CIC weight derivatives (mesh planes) and of the pair force at r_c are not differentiated.
+ * p3m_density_loss: *loss = sum_nodes (delta - target)^2 with delta = n/n_bar - 1 the CIC
+ *   density contrast of the current positions on the M^3 mesh, target[M^3] doubles (index
+ *   (ix*M + iy)*M + iz); grad3n (nullable) = dL/dx [3][n].  Synchronises (loss is a host
+ *   pointer).
+ * p3m_axpy: y3n += alpha x3n over 3n doubles (device arrays).
+ * p3m_step_factors: the step's kick factors m K(a, a+da/2), m K(a+da/2, a+da) and drift factor
+ *   D(a, a+da)/m, as p3m_step uses them.
+ * Pointers follow on_device as elsewhere (p3m_axpy: device only).
+ */
+int p3m_force_vjp(p3m_ctx *ctx, const double *v3n, double *out3n, int on_device);
+int p3m_density_loss(p3m_ctx *ctx, const double *target, double *loss, double *grad3n,
+                     int on_device);
+int p3m_axpy(p3m_ctx *ctx, double alpha, const double *x3n, double *y3n);
+int p3m_step_factors(const p3m_ctx *ctx, double a, double da, double *k1, double *dfac,
+                     double *k2);
+
 /* Momentum, kinetic energy, pair count and cell statistics of the current state.
  * Synchronises the stream. */
 int p3m_diagnostics(p3m_ctx *ctx, p3m_diag *out);

@@ -116,6 +116,7 @@ class P3M:
 
     # ------------------------------------------------------------------ particles
     def set_particles(self, pos, mom, acc=None, mass: float = 1.0, a: float = 1.0):
+        self.mass = float(mass)
         s = (3, self.n)
         p, d1 = _addr(pos, s, "float64")
         m, d2 = _addr(mom, s, "float64")
@@ -171,6 +172,37 @@ class P3M:
                                                  float(tophat_radius), k.ctypes.data,
                                                  p.ctypes.data, c.ctypes.data, ctypes.byref(s)))
         return k, p, c, (s.value if tophat_radius > 0 else None)
+
+    def force_vjp(self, v, out=None):
+        """(dA/dx)^T v at the current positions (v, out: (3, N) float64, host or device)."""
+        if out is None:
+            out = np.empty((3, self.n)) if not _is_torch(v) else v.new_empty((3, self.n))
+        a, d1 = _addr(v, (3, self.n), "float64")
+        b, d2 = _addr(out, (3, self.n), "float64")
+        self._check(self._lib.p3m_force_vjp(self._ctx, a, b, _side(d1, d2)))
+        return out
+
+    def density_loss(self, target, grad=None):
+        """(loss, grad): L2 of the CIC density contrast against target (M^3 float64)."""
+        t, d1 = _addr(target, (self.mesh ** 3,), "float64")
+        g, d2 = _addr(grad, (3, self.n), "float64")
+        loss = ctypes.c_double()
+        self._check(self._lib.p3m_density_loss(self._ctx, t, ctypes.byref(loss), g, _side(d1, d2)))
+        return loss.value, grad
+
+    def axpy(self, alpha: float, x, y):
+        """y += alpha x on (3, N) float64 device tensors."""
+        a, d1 = _addr(x, (3, self.n), "float64")
+        b, d2 = _addr(y, (3, self.n), "float64")
+        if not (d1 and d2):
+            raise ValueError("axpy works on device tensors")
+        self._check(self._lib.p3m_axpy(self._ctx, float(alpha), a, b))
+
+    def step_factors(self, a: float, da: float):
+        k1, d, k2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.p3m_step_factors(self._ctx, float(a), float(da), ctypes.byref(k1),
+                                               ctypes.byref(d), ctypes.byref(k2)))
+        return k1.value, d.value, k2.value
 
     def run_steps(self, a_list, use_graph: bool = True):
         """Kick-drift-kick steps through the scale factors a_list (len = steps + 1), replayed

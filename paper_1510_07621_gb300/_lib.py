@@ -70,6 +70,11 @@ SIGNATURES = {
     "p3m_set_timing": (_c.c_int, [_vp, _c.c_int]),
     "p3m_timings": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.c_int, _c.c_int]),
     "p3m_phase_name": (_c.c_char_p, [_c.c_int]),
+    "p3m_force_vjp": (_c.c_int, [_vp, _vp, _vp, _c.c_int]),
+    "p3m_density_loss": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double), _vp, _c.c_int]),
+    "p3m_axpy": (_c.c_int, [_vp, _c.c_double, _vp, _vp]),
+    "p3m_step_factors": (_c.c_int, [_vp, _c.c_double, _c.c_double, _c.POINTER(_c.c_double),
+                                    _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
     "p3m_run_steps": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int]),
     "p3m_set_stream": (_c.c_int, [_vp, _vp]),
     "p3m_ensemble_create": (_c.c_int, [_c.POINTER(_vp), _vp, _c.c_int, _c.c_int]),

@@ -1,0 +1,451 @@
+// Reverse-mode derivative of the P3M force: the transposed Jacobian of the accelerations
+// applied to a vector field v, (dA/dx)^T v, and the gradient of a mesh density loss.  These
+// are the pieces of the adjoint of the kick-drift-kick step (the reverse sweep itself runs on
+// the host side).
+//
+// Mesh part, with E_b = D_b rho the three mesh accelerations (D_b = IFFT(-i k_b G FFT), real,
+// D_b^T = IFFT(+i k_b G FFT)) and rho(n) = sum_j W(x_j - n) the CIC counts:
+//   out_k = sum_n grad W(x_k - n) [ sum_b v_k,b E_b(n) + psi(n) ],
+//   psi = sum_b D_b^T u_b,  u_b(n) = sum_i W(x_i - n) v_i,b.
+// Pair part, J(d) = h(r) I + (h'(r)/r) d d^T with h(r) = Gm g(r/r_s) (r^2 + eps^2)^-3/2:
+//   out_k = sum_{j: 0 < r_kj < r_c} J(d_kj) (v_j - v_k).
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <math.h>
+
+#include "p3m_internal.cuh"
+
+namespace {
+
+inline int grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t b = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)num_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ int wrap_index(int i, int M)
+{
+    i %= M;
+    return i < 0 ? i + M : i;
+}
+
+// CIC stencil in FP64: base node i0 = floor(x M/L), fraction f.
+__device__ __forceinline__ void stencil64(double x, double inv_h, int &i0, double &f)
+{
+    const double u = __dmul_rn(x, inv_h);
+    const double fl = floor(u);
+    i0 = (int)fl;
+    f = u - fl;
+}
+
+// v_sorted[k] = v[pid[k]] (caller order -> slot order), also an FP32 copy with w = 0.
+__global__ void k_to_slots(const double *__restrict__ v, const uint32_t *__restrict__ pid,
+                           int64_t n, double *__restrict__ vs, float4 *__restrict__ vf)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = pid[k];
+        const double a = v[j], b = v[n + j], c = v[2 * n + j];
+        vs[k] = a;
+        vs[n + k] = b;
+        vs[2 * n + k] = c;
+        vf[k] = make_float4((float)a, (float)b, (float)c, 0.0f);
+    }
+}
+
+// u_b(node) += W(x_k - node) v_k,b, three meshes of type T.
+template <typename T>
+__global__ void k_deposit_vec(const double *__restrict__ pos, const double *__restrict__ v,
+                              P3MGeom g, T *__restrict__ u)
+{
+    const int M = g.mesh;
+    const int64_t n = g.n;
+    const size_t M3 = (size_t)M * M * M;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        double fx, fy, fz;
+        stencil64(pos[k], g.inv_h, ix, fx);
+        stencil64(pos[n + k], g.inv_h, iy, fy);
+        stencil64(pos[2 * n + k], g.inv_h, iz, fz);
+        const double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
+        const double vb[3] = {v[k], v[n + k], v[2 * n + k]};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const double w = wx[a] * wy[b] * wz[c];
+                    const size_t node = ((size_t)wrap_index(ix + a, M) * M + wrap_index(iy + b, M)) * M +
+                                        wrap_index(iz + c, M);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) atomicAdd(u + d * M3 + node, (T)(w * vb[d]));
+                }
+    }
+}
+
+// psi_k = sum_b (+i kg_b G(k)) u_b,k with G as in the forward pass (constants included).
+template <typename T, typename C2>
+__global__ void k_kspace_adjoint(const C2 *__restrict__ ux, const C2 *__restrict__ uy,
+                                 const C2 *__restrict__ uz, const T *__restrict__ tk,
+                                 const T *__restrict__ tkg, const T *__restrict__ tg, int M,
+                                 T gconst, C2 *__restrict__ psi)
+{
+    const int nz = M / 2 + 1;
+    const size_t total = (size_t)M * M * nz;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int iz = (int)(idx % nz);
+        const size_t t = idx / nz;
+        const int iy = (int)(t % M), ix = (int)(t / M);
+        const T kx = tk[ix], ky = tk[iy], kz = tk[iz];
+        const T k2 = kx * kx + ky * ky + kz * kz;
+        const T G = idx == 0 ? T(0) : gconst * (tg[ix] * tg[iy] * tg[iz]) / k2;
+        const C2 a = ux[idx], b = uy[idx], c = uz[idx];
+        // i kg G u = G kg (-u.y, u.x)
+        const T gx = G * tkg[ix], gy = G * tkg[iy], gz = G * tkg[iz];
+        C2 o;
+        o.x = -(gx * a.y + gy * b.y + gz * c.y);
+        o.y = gx * a.x + gy * b.x + gz * c.x;
+        psi[idx] = o;
+    }
+}
+
+// out_k += scale sum_corners grad W(x_k - node) [ sum_b v_k,b E_b(node) + psi(node) ]
+// (E or v NULL: no first term; psi NULL: no second term).
+template <typename T>
+__global__ void k_gather_grad(const double *__restrict__ pos, P3MGeom g, const T *__restrict__ E,
+                              const double *__restrict__ v, const T *__restrict__ psi,
+                              double scale, double *__restrict__ out)
+{
+    const int M = g.mesh;
+    const int64_t n = g.n;
+    const size_t M3 = (size_t)M * M * M;
+    const double ih = g.inv_h;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int ix, iy, iz;
+        double fx, fy, fz;
+        stencil64(pos[k], ih, ix, fx);
+        stencil64(pos[n + k], ih, iy, fy);
+        stencil64(pos[2 * n + k], ih, iz, fz);
+        const double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
+        const double dx[2] = {-ih, ih};
+        double vb[3] = {0.0, 0.0, 0.0};
+        if (E && v) {
+            vb[0] = v[k];
+            vb[1] = v[n + k];
+            vb[2] = v[2 * n + k];
+        }
+        double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const size_t node = ((size_t)wrap_index(ix + a, M) * M + wrap_index(iy + b, M)) * M +
+                                        wrap_index(iz + c, M);
+                    double s = psi ? (double)psi[node] : 0.0;
+                    if (E && v)
+                        s += vb[0] * (double)E[node] + vb[1] * (double)E[M3 + node] +
+                             vb[2] * (double)E[2 * M3 + node];
+                    o0 += dx[a] * wy[b] * wz[c] * s;
+                    o1 += wx[a] * dx[b] * wz[c] * s;
+                    o2 += wx[a] * wy[b] * dx[c] * s;
+                }
+        out[k] += scale * o0;
+        out[n + k] += scale * o1;
+        out[2 * n + k] += scale * o2;
+    }
+}
+
+// Density loss on the mesh: rho holds counts - mean; delta = rho / n_bar; per node
+// r = delta - target; loss partial sums per block; ell = 2 r / n_bar written over rho.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_loss_mesh(T *__restrict__ rho, const double *__restrict__ target, size_t M3, double inv_nbar,
+                double *__restrict__ part)
+{
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < M3;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double r = (double)rho[i] * inv_nbar - target[i];
+        acc += r * r;
+        rho[i] = (T)(2.0 * r * inv_nbar);
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_sum_parts(double *part, int nb, double *out)
+{
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// ------------------------------------------------------------------ pair part
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct GPolyA {
+    float c[12];
+};
+
+// h(r)/Gm and h'(r)/(Gm r) for one pair (FP32): g from the fitted polynomial, g' in closed form.
+__device__ __forceinline__ void pair_jac(float r2, float eps2, float inv_rs, const GPolyA &gp,
+                                         float &h, float &hr)
+{
+    const float t = rsqrt_approx(r2);
+    const float s = rsqrt_approx(r2 + eps2);
+    const float r = r2 * t;
+    const float tau = fmaf(r2, gp.c[11], -1.0f);
+    float p = gp.c[10];
+#pragma unroll
+    for (int k = 9; k >= 0; --k) p = fmaf(p, tau, gp.c[k]);
+    const float gval = fmaf(r2 * r, p, 1.0f);
+    const float x = r * inv_rs;
+    const float gder = -x * x * __expf(-0.25f * x * x) * 0.282094791773878143f;  // 1/(2 sqrt pi)
+    const float s3 = s * s * s;
+    h = gval * s3;
+    // h' / r = [g'/r_s s^3 - 3 r g s^5] / r
+    hr = gder * inv_rs * s3 * t - 3.0f * gval * s3 * s * s;
+}
+
+__device__ __forceinline__ void pair_jac(double r2, double eps2, double inv_rs, const GPolyA &,
+                                         double &h, double &hr)
+{
+    const double r = sqrt(r2), x = r * inv_rs;
+    const double s2 = r2 + eps2, s3 = s2 * sqrt(s2);
+    const double gval = erfc(0.5 * x) + x * 0.56418958354775628695 * exp(-0.25 * x * x);
+    const double gder = -x * x * exp(-0.25 * x * x) * 0.28209479177387814347;
+    h = gval / s3;
+    hr = (gder * inv_rs / s3 - 3.0 * r * gval / (s3 * s2)) / r;
+}
+
+template <typename T>
+struct V4Of;
+template <>
+struct V4Of<float> {
+    using type = float4;
+};
+template <>
+struct V4Of<double> {
+    using type = double4;
+};
+
+// One warp per work item (up to 32 particles of one cell); j particles read through the
+// cache.  out_k += Gm sum_j J(d_kj) (v_j - v_k).
+template <typename T>
+__global__ void __launch_bounds__(32)
+    k_pairs_vjp(const typename V4Of<T>::type *__restrict__ rel, const float4 *__restrict__ vf,
+                const double *__restrict__ vs, const uint32_t *__restrict__ cell_start,
+                const uint32_t *__restrict__ work, const uint32_t *__restrict__ n_work_ptr,
+                P3MGeom g, GPolyA gp, uint32_t *__restrict__ cursor, double *__restrict__ out)
+{
+    using V4 = typename V4Of<T>::type;
+    constexpr bool kAbsolute = sizeof(T) == 8;
+    const int lane = threadIdx.x;
+    const int64_t n = g.n;
+    const uint32_t n_work = *n_work_ptr;
+    const T rc2 = (T)(g.r_c * g.r_c), eps2 = (T)(g.eps * g.eps), inv_rs = (T)(1.0 / g.r_s);
+    const int nc = g.n_c;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(cursor, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_work) break;
+        const uint32_t cell = work[2 * (size_t)item], first = work[2 * (size_t)item + 1];
+        const uint32_t cend = cell_start[cell + 1];
+        const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
+        const uint32_t i = first + lane;
+        const bool valid = i < cend;
+        const uint32_t ii = valid ? i : first;
+        const V4 xi = rel[ii];
+        const double vix = vs[ii], viy = vs[n + ii], viz = vs[2 * n + ii];
+        double o[3] = {0.0, 0.0, 0.0};
+        for (int nb = 0; nb < 27; ++nb) {
+            const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
+            const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
+            const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
+            const double L = g.box, cs = g.cs;
+            const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+            const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+            const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            T xs, ys, zs, ix = 0, iy = 0, iz = 0;
+            if (kAbsolute) {
+                xs = (T)xi.x;
+                ys = (T)xi.y;
+                zs = (T)xi.z;
+                ix = (T)imx;
+                iy = (T)imy;
+                iz = (T)imz;
+            } else {
+                xs = (T)((double)xi.x - (((double)wx * cs + imx) - (double)cx * cs));
+                ys = (T)((double)xi.y - (((double)wy * cs + imy) - (double)cy * cs));
+                zs = (T)((double)xi.z - (((double)wz * cs + imz) - (double)cz * cs));
+            }
+            T ox = 0, oy = 0, oz = 0;
+            for (uint32_t j = cell_start[q]; j < cell_start[q + 1]; ++j) {
+                const V4 qj = rel[j];
+                T dx = qj.x - xs, dy = qj.y - ys, dz = qj.z - zs;
+                if (kAbsolute) {
+                    dx += ix;
+                    dy += iy;
+                    dz += iz;
+                }
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                const bool in = valid && r2 < rc2 && r2 > T(0);
+                if (!__any_sync(0xffffffffu, in)) continue;
+                T h, hr;
+                pair_jac(r2, eps2, inv_rs, gp, h, hr);
+                T w0, w1, w2;
+                if (kAbsolute) {
+                    w0 = (T)(vs[j] - vix);
+                    w1 = (T)(vs[n + j] - viy);
+                    w2 = (T)(vs[2 * n + j] - viz);
+                } else {
+                    const float4 vj = vf[j];
+                    w0 = (T)((double)vj.x - vix);
+                    w1 = (T)((double)vj.y - viy);
+                    w2 = (T)((double)vj.z - viz);
+                }
+                const T dw = dx * w0 + dy * w1 + dz * w2;
+                const T c = in ? hr * dw : T(0);
+                const T hh = in ? h : T(0);
+                ox += hh * w0 + c * dx;
+                oy += hh * w1 + c * dy;
+                oz += hh * w2 + c * dz;
+            }
+            o[0] += (double)ox;
+            o[1] += (double)oy;
+            o[2] += (double)oz;
+        }
+        if (valid) {
+            out[i] += g.gm * o[0];
+            out[n + i] += g.gm * o[1];
+            out[2 * n + i] += g.gm * o[2];
+        }
+    }
+}
+
+template <typename T, typename C2>
+cudaError_t vjp_mesh(p3m_ctx *c, const double *v_slots, double *out_slots)
+{
+    const int M = c->g.mesh;
+    const size_t M3 = (size_t)M * M * M, nk = (size_t)M * M * (M / 2 + 1);
+    T *u = (T *)c->adj_u;
+    cudaError_t e = cudaMemsetAsync(u, 0, 3 * M3 * sizeof(T), c->stream);
+    if (e != cudaSuccess) return e;
+    c->launches += 3;
+    k_deposit_vec<T><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(c->pos, v_slots, c->g, u);
+    C2 *uk = (C2 *)c->frc_k;
+    for (int b = 0; b < 3; ++b) {
+        cufftResult r = sizeof(T) == 4
+                            ? cufftExecR2C(c->plan_r2c, (cufftReal *)(u + b * M3), (cufftComplex *)(uk + b * nk))
+                            : cufftExecD2Z(c->plan_r2c, (cufftDoubleReal *)(u + b * M3),
+                                           (cufftDoubleComplex *)(uk + b * nk));
+        if (r != CUFFT_SUCCESS) return cudaErrorUnknown;
+    }
+    C2 *psik = (C2 *)c->rho_k;
+    k_kspace_adjoint<T, C2><<<grid_for((int64_t)nk, 256, c->num_sms), 256, 0, c->stream>>>(
+        uk, uk + nk, uk + 2 * nk, (const T *)c->tab_k, (const T *)c->tab_kg, (const T *)c->tab_g, M,
+        (T)c->green_const, psik);
+    T *psi = (T *)c->rho;
+    cufftResult r = sizeof(T) == 4 ? cufftExecC2R(c->plan_c2r_one, (cufftComplex *)psik, (cufftReal *)psi)
+                                   : cufftExecZ2D(c->plan_c2r_one, (cufftDoubleComplex *)psik,
+                                                  (cufftDoubleReal *)psi);
+    if (r != CUFFT_SUCCESS) return cudaErrorUnknown;
+    k_gather_grad<T><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+        c->pos, c->g, (const T *)c->frc, v_slots, psi, 1.0, out_slots);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vjp_pairs(p3m_ctx *c, const double *v_slots, double *out_slots)
+{
+    GPolyA gp;
+    for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_vjp<T>, 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    e = cudaMemsetAsync(c->counters + 3, 0, sizeof(uint32_t), c->stream);
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+    k_pairs_vjp<T><<<c->num_sms * per_sm, 32, 0, c->stream>>>(
+        (const typename V4Of<T>::type *)c->rel, c->adj_vf, v_slots, c->cell_start, c->work,
+        c->work_off + c->g.n_cells, c->g, gp, c->counters + 3, out_slots);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_to_slots(p3m_ctx *c, const double *v, double *vs)
+{
+    c->launches += 1;
+    k_to_slots<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(v, c->pid, c->g.n, vs, c->adj_vf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_vjp(p3m_ctx *c, const double *v_slots, double *out_slots)
+{
+    cudaError_t e = cudaMemsetAsync(out_slots, 0, 3 * sizeof(double) * c->g.n, c->stream);
+    if (e != cudaSuccess) return e;
+    if (c->precision == P3M_PREC_MIXED) {
+        e = vjp_mesh<float, cufftComplex>(c, v_slots, out_slots);
+        if (e == cudaSuccess && c->short_range) e = vjp_pairs<float>(c, v_slots, out_slots);
+    } else {
+        e = vjp_mesh<double, cufftDoubleComplex>(c, v_slots, out_slots);
+        if (e == cudaSuccess && c->short_range) e = vjp_pairs<double>(c, v_slots, out_slots);
+    }
+    return e;
+}
+
+cudaError_t launch_density_loss(p3m_ctx *c, const double *target, double *loss_dev, double *grad_slots)
+{
+    const int M = c->g.mesh;
+    const size_t M3 = (size_t)M * M * M;
+    const double inv_nbar = 1.0 / c->g.mean_count;
+    const int nb = 1024;
+    c->launches += 2;
+    if (c->precision == P3M_PREC_MIXED)
+        k_loss_mesh<float><<<nb, 256, 0, c->stream>>>((float *)c->rho, target, M3, inv_nbar, c->red);
+    else
+        k_loss_mesh<double><<<nb, 256, 0, c->stream>>>((double *)c->rho, target, M3, inv_nbar, c->red);
+    k_sum_parts<<<1, 256, 0, c->stream>>>(c->red, nb, loss_dev);
+    if (grad_slots) {
+        cudaError_t e = cudaMemsetAsync(grad_slots, 0, 3 * sizeof(double) * c->g.n, c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 1;
+        if (c->precision == P3M_PREC_MIXED)
+            k_gather_grad<float><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+                c->pos, c->g, nullptr, nullptr, (const float *)c->rho, 1.0, grad_slots);
+        else
+            k_gather_grad<double><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+                c->pos, c->g, nullptr, nullptr, (const double *)c->rho, 1.0, grad_slots);
+    }
+    return cudaGetLastError();
+}

@@ -186,12 +186,14 @@ void release(p3m_ctx *c)
                     c->red,       c->rho,      c->rho_k,        c->frc_k,    c->frc,
                     c->tab_k,     c->tab_kg,   c->tab_g,        c->work_key, c->work_key_alt,
                     c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
-                    c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac};
+                    c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac,
+                    c->adj_u,     c->adj_vf,   c->adj_vs,       c->adj_out};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
         cufftDestroy(c->plan_r2c);
         cufftDestroy(c->plan_c2r);
+        cufftDestroy(c->plan_c2r_one);
     }
     if (c->ev) {
         for (int i = 0; i < c->ev_cap; ++i) cudaEventDestroy(c->ev[i]);
@@ -220,7 +222,8 @@ int check_flags(p3m_ctx *c)
 // Sort by cell, mesh force, pair force.  Positions must already be wrapped and keyed
 // (c->keys).  Result: c->acc (total), c->acc_lr (mesh part).  kfac != 0: the final half kick
 // mom += kfac * acc is fused into the last kernel.
-int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table = false)
+int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table = false,
+             bool pairs = true)
 {
     const double *kfac_dev = from_table ? c->cur_fac + 2 : nullptr;
     {
@@ -252,7 +255,10 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table = fal
                 ? cufftExecC2R(c->plan_c2r, (cufftComplex *)c->frc_k, (cufftReal *)c->frc)
                 : cufftExecZ2D(c->plan_c2r, (cufftDoubleComplex *)c->frc_k, (cufftDoubleReal *)c->frc));
     }
-    if (c->short_range) {
+    if (c->short_range && !pairs) {  // mesh part only (cells, sorted state, mesh fields)
+        Phase ph(c, PH_GATHER);
+        CK(launch_gather(c, c->acc_lr));
+    } else if (c->short_range) {
         {
             Phase ph(c, PH_GATHER);
             CK(launch_gather(c, c->acc_lr));
@@ -496,6 +502,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->tab_one, 8 * M},    {(void **)&c->ps_acc, 8 * (3 * (M / 2) + 1)},
             {(void **)&c->fac_table, 8 * 3 * (size_t)P3M_MAX_GRAPH_STEPS},
             {(void **)&c->step_idx, 16},      {(void **)&c->cur_fac, 32},
+            {(void **)&c->adj_u, 3 * real * M3}, {(void **)&c->adj_vf, 16 * N},
+            {(void **)&c->adj_vs, 24 * N},    {(void **)&c->adj_out, 24 * N},
         };
         for (auto &a : allocs) {
             e = dalloc(a.p, a.bytes);
@@ -565,6 +573,14 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
                               c->precision == P3M_PREC_MIXED ? CUFFT_C2R : CUFFT_Z2D, 3);
             if (r != CUFFT_SUCCESS) cufftDestroy(c->plan_r2c);
         }
+        if (r == CUFFT_SUCCESS) {
+            r = cufftPlan3d(&c->plan_c2r_one, mesh, mesh, mesh,
+                            c->precision == P3M_PREC_MIXED ? CUFFT_C2R : CUFFT_Z2D);
+            if (r != CUFFT_SUCCESS) {
+                cufftDestroy(c->plan_r2c);
+                cufftDestroy(c->plan_c2r);
+            }
+        }
         if (r != CUFFT_SUCCESS) {
             rc = fail(nullptr, P3M_ECUFFT, "p3m_init: cuFFT plan creation failed (code %d)", (int)r);
             break;
@@ -572,6 +588,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         c->plans_made = true;
         cufftSetStream(c->plan_r2c, c->stream);
         cufftSetStream(c->plan_c2r, c->stream);
+        cufftSetStream(c->plan_c2r_one, c->stream);
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             rc = fail(nullptr, P3M_ECUDA, "p3m_init: %s", cudaGetErrorString(e));
@@ -859,6 +876,7 @@ extern "C" int p3m_set_stream(p3m_ctx *c, void *stream)
     c->stream = (cudaStream_t)stream;
     CKF(cufftSetStream(c->plan_r2c, c->stream));
     CKF(cufftSetStream(c->plan_c2r, c->stream));
+    CKF(cufftSetStream(c->plan_c2r_one, c->stream));
     return P3M_OK;
 }
 
@@ -1151,5 +1169,79 @@ extern "C" int p3m_autotune(p3m_ctx *c, int *sub_bits_out, double *ms_out)
     if (rc) return rc;
     c->forces_valid = true;
     if (sub_bits_out) *sub_bits_out = best_b;
+    return P3M_OK;
+}
+
+// ---------------------------------------------------------------- reverse-mode derivatives
+
+extern "C" int p3m_step_factors(const p3m_ctx *c, double a, double da, double *k1, double *dfac,
+                                double *k2)
+{
+    if (!c || !finite_pos(a) || !finite_pos(da)) return P3M_EINVAL;
+    const double am = a + 0.5 * da, a2 = a + da;
+    if (k1) *k1 = c->mass * p3m_kick_factor(c->cosmo, a, am);
+    if (dfac) *dfac = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
+    if (k2) *k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+    return P3M_OK;
+}
+
+extern "C" int p3m_axpy(p3m_ctx *c, double alpha, const double *x3n, double *y3n)
+{
+    if (!c || !x3n || !y3n) return fail(c, P3M_EINVAL, "p3m_axpy: NULL argument");
+    CK(launch_axpy(c, y3n, x3n, alpha));
+    return P3M_OK;
+}
+
+extern "C" int p3m_force_vjp(p3m_ctx *c, const double *v3n, double *out3n, int on_device)
+{
+    if (!c || !v3n || !out3n) return fail(c, P3M_EINVAL, "p3m_force_vjp: NULL argument");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_force_vjp: no particles loaded");
+    const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
+    // sort, cells and mesh fields at the current positions (the pair forces are not needed)
+    int rc = key_current(c);
+    if (!rc) rc = evaluate(c, 0.0, nullptr, false, false);
+    if (rc) return rc;
+    c->forces_valid = !c->short_range;
+    const double *vin = v3n;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->pos_alt, v3n, bytes, cudaMemcpyHostToDevice, c->stream));
+        vin = c->pos_alt;
+    }
+    CK(launch_to_slots(c, vin, c->adj_vs));
+    CK(launch_force_vjp(c, c->adj_vs, c->adj_out));
+    if (on_device) {
+        CK(launch_scatter_out(c, c->adj_out, out3n));
+        return P3M_OK;
+    }
+    CK(launch_scatter_out(c, c->adj_out, c->pos_alt));
+    CK(cudaMemcpyAsync(out3n, c->pos_alt, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return check_flags(c);
+}
+
+extern "C" int p3m_density_loss(p3m_ctx *c, const double *target, double *loss, double *grad3n,
+                                int on_device)
+{
+    if (!c || !target || !loss) return fail(c, P3M_EINVAL, "p3m_density_loss: NULL argument");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_density_loss: no particles loaded");
+    const size_t M3 = (size_t)c->g.mesh * c->g.mesh * c->g.mesh;
+    const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
+    const double *t = target;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(c->adj_u, target, sizeof(double) * M3, cudaMemcpyHostToDevice, c->stream));
+        t = (const double *)c->adj_u;
+    }
+    CK(launch_deposit(c));
+    double *loss_dev = c->red + 1024 * 4 + 4;
+    CK(launch_density_loss(c, t, loss_dev, grad3n ? c->adj_out : nullptr));
+    if (grad3n) {
+        if (on_device) {
+            CK(launch_scatter_out(c, c->adj_out, grad3n));
+        } else {
+            CK(launch_scatter_out(c, c->adj_out, c->pos_alt));
+            CK(cudaMemcpyAsync(grad3n, c->pos_alt, bytes, cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    CK(cudaMemcpyAsync(loss, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return P3M_OK;
 }

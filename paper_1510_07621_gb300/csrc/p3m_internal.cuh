@@ -70,7 +70,7 @@ struct p3m_ctx {
     double green_const;
     float gpoly[12];  // FP32 split factor: g = 1 + x u Q(tau), Q = sum gpoly[k] tau^k (k <= 10),
                       // tau = u gpoly[11] - 1, u = (r/r_s)^2
-    cufftHandle plan_r2c, plan_c2r;
+    cufftHandle plan_r2c, plan_c2r, plan_c2r_one;  // R2C, batched 3 x C2R, single C2R
     bool plans_made;
 
     // timing
@@ -89,6 +89,12 @@ struct p3m_ctx {
     bool capturing;
     int geom_version;              // bumped when the geometry changes (captured graphs go stale)
     struct p3m_ensemble *self_ens;  // private one-context ensemble of p3m_run_steps
+
+    // reverse-mode derivative buffers
+    void *adj_u;       // three real meshes (vector deposit; also target-mesh staging)
+    float4 *adj_vf;    // v in slot order, FP32
+    double *adj_vs;    // v in slot order, FP64 [3][n]
+    double *adj_out;   // result in slot order [3][n]
 
     bool have_particles;
     bool forces_valid;
@@ -153,6 +159,14 @@ cudaError_t launch_load_particles(p3m_ctx *c, const double *pos, const double *m
                                   const double *acc);
 cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst);
 cudaError_t launch_diag(p3m_ctx *c, double *host_out /* [4]: px py pz 2*kinetic*m*a^2 */);
+
+// ------------------------------------------------------------------ launchers (adjoint.cu)
+// vs (and adj_vf) = v permuted from caller order into slot order
+cudaError_t launch_to_slots(p3m_ctx *c, const double *v, double *vs);
+// out_slots = (dA/dx)^T v_slots at the current (sorted, evaluated) state
+cudaError_t launch_force_vjp(p3m_ctx *c, const double *v_slots, double *out_slots);
+// loss_dev = sum (rho/n_bar - target)^2 over the deposited mesh; grad_slots (nullable) = dL/dx
+cudaError_t launch_density_loss(p3m_ctx *c, const double *target, double *loss_dev, double *grad_slots);
 
 // host helpers (api.cu)
 // Records a message for p3m_last_error(NULL) and returns code.
