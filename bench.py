@@ -448,6 +448,56 @@ def run_ensemble(args):
             "speedup_graph_over_serial": value / out["serial_host_launches"]}
 
 
+# ---------------------------------------------------------------- differentiable run
+
+
+ADJOINT_NAME = ("adjoint128: 128^3 particles, 128^3 mesh, box 200 Mpc/h, 20 log steps a=0.05->1, "
+                "L2 loss of the final CIC density contrast against a seeded target, gradient with "
+                "respect to the 128^3 initial displacement field, checkpoints every 5 steps")
+
+
+def run_adjoint(args):
+    """Forward run + loss, then the reverse sweep (checkpoints every sqrt(20) ~ 5 steps):
+    cost of the gradient per step relative to a forward step."""
+    import torch
+    from paper_1510_07621_gb300 import P3M, build
+    from paper_1510_07621_gb300.adjoint import DensityLossRun
+
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n_p, box, mesh = 128, 200.0, 128
+    q = torch.from_numpy(S.lattice(n_p, box)).to(dev)
+    _, mom = S.zeldovich(n_p, box, 0.05, 1515)
+    psi = torch.from_numpy(mom / np.sqrt(0.05)).to(dev)
+    a = S.log_spaced_steps(0.05, 1.0, 20)
+    target = torch.from_numpy(0.5 * S.gaussian(1516, mesh ** 3)).to(dev)
+    sim = P3M(box, n_p ** 3, mesh, softening=0.02)
+    # warm-up (plans, first-touch)
+    x = psi.clone().requires_grad_(True)
+    DensityLossRun.apply(x, sim, q, a[:3], target, 2).backward()
+    torch.cuda.synchronize()
+    x = psi.clone().requires_grad_(True)
+    t0 = time.perf_counter()
+    loss = DensityLossRun.apply(x, sim, q, a, target, 5)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = x.grad
+    fwd, bwd = (t1 - t0) / 20, (t2 - t1) / 20
+    sim.close()
+    return {"metric": METRIC, "value": n_p ** 3 / bwd, "unit": UNIT + " (reverse sweep)",
+            "n_gpus": 1, "steps": 20, "warmup": 1, "ms_per_step": 1e3 * bwd,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 forces, f64 positions/momenta", "data": "synthetic",
+            "config": {"workload": ADJOINT_NAME, "particles": n_p ** 3},
+            "forward_ms_per_step": 1e3 * fwd, "adjoint_ms_per_step": 1e3 * bwd,
+            "adjoint_over_forward": bwd / fwd, "loss": float(loss.detach()),
+            "grad_rms": float(g.pow(2).mean().sqrt())}
+
+
 # ---------------------------------------------------------------- reference arm (oracle)
 
 
@@ -487,7 +537,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--workload", choices=["clustered_128", "ensemble48"], default="clustered_128")
+    ap.add_argument("--workload", choices=["clustered_128", "ensemble48", "adjoint128"],
+                    default="clustered_128")
     ap.add_argument("--sub-bits", type=int, default=None,
                     help="Morton bits per axis inside a chaining cell (library default if unset)")
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -507,9 +558,10 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.workload == "ensemble48":
+    if args.workload in ("ensemble48", "adjoint128"):
         if rank == 0:
-            print(json.dumps(run_ensemble(args)), flush=True)
+            fn = run_ensemble if args.workload == "ensemble48" else run_adjoint
+            print(json.dumps(fn(args)), flush=True)
         return
 
     dist = None

@@ -256,14 +256,19 @@ struct V4Of<double> {
     using type = double4;
 };
 
-// One warp per work item (up to 32 particles of one cell); j particles read through the
-// cache.  out_k += Gm sum_j J(d_kj) (v_j - v_k).
+// One warp per work item (up to 32 particles of one cell, most expensive items first), like
+// the force pair kernel: the j particles of the 27 neighbour cells in 32-slot blocks, a block
+// skipped when no lane's particle is within r_c of its bounding box, evaluated without pair
+// tests when it lies within r_c of every lane's particle.  j data read through the cache.
+// out_k += Gm sum_j J(d_kj) (v_j - v_k).
 template <typename T>
 __global__ void __launch_bounds__(32)
-    k_pairs_vjp(const typename V4Of<T>::type *__restrict__ rel, const float4 *__restrict__ vf,
+    k_pairs_vjp(const typename V4Of<T>::type *__restrict__ rel, const double *__restrict__ pos,
+                const float4 *__restrict__ block_box, const float4 *__restrict__ vf,
                 const double *__restrict__ vs, const uint32_t *__restrict__ cell_start,
-                const uint32_t *__restrict__ work, const uint32_t *__restrict__ n_work_ptr,
-                P3MGeom g, GPolyA gp, uint32_t *__restrict__ cursor, double *__restrict__ out)
+                const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
+                const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPolyA gp, float rcull2,
+                float rin2, uint32_t *__restrict__ cursor, double *__restrict__ out)
 {
     using V4 = typename V4Of<T>::type;
     constexpr bool kAbsolute = sizeof(T) == 8;
@@ -273,10 +278,11 @@ __global__ void __launch_bounds__(32)
     const T rc2 = (T)(g.r_c * g.r_c), eps2 = (T)(g.eps * g.eps), inv_rs = (T)(1.0 / g.r_s);
     const int nc = g.n_c;
     for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(cursor, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= n_work) break;
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(cursor, 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= n_work) break;
+        const uint32_t item = order[slot];
         const uint32_t cell = work[2 * (size_t)item], first = work[2 * (size_t)item + 1];
         const uint32_t cend = cell_start[cell + 1];
         const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
@@ -284,12 +290,15 @@ __global__ void __launch_bounds__(32)
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
         const V4 xi = rel[ii];
-        const double vix = vs[ii], viy = vs[n + ii], viz = vs[2 * n + ii];
+        const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];
+        const T vix = (T)vs[ii], viy = (T)vs[n + ii], viz = (T)vs[2 * n + ii];
         double o[3] = {0.0, 0.0, 0.0};
         for (int nb = 0; nb < 27; ++nb) {
             const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
             const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
             const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
+            const uint32_t js = cell_start[q], je = cell_start[q + 1];
+            if (js == je) continue;
             const double L = g.box, cs = g.cs;
             const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
             const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
@@ -307,37 +316,59 @@ __global__ void __launch_bounds__(32)
                 ys = (T)((double)xi.y - (((double)wy * cs + imy) - (double)cy * cs));
                 zs = (T)((double)xi.z - (((double)wz * cs + imz) - (double)cz * cs));
             }
+            const float cxs = (float)(xa - imx), cys = (float)(ya - imy), czs = (float)(za - imz);
             T ox = 0, oy = 0, oz = 0;
-            for (uint32_t j = cell_start[q]; j < cell_start[q + 1]; ++j) {
-                const V4 qj = rel[j];
-                T dx = qj.x - xs, dy = qj.y - ys, dz = qj.z - zs;
+            for (uint32_t b = js >> 5; b * 32u < je; ++b) {
+                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
+                const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
+                const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
+                if (!__any_sync(0xffffffffu, valid && ex * ex + ey * ey + ez * ez < rcull2)) continue;
+                const float fx = fmaxf(cxs - lo.x, hi.x - cxs);
+                const float fy = fmaxf(cys - lo.y, hi.y - cys);
+                const float fz = fmaxf(czs - lo.z, hi.z - czs);
+                const bool all_in =
+                    __all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2);
+                const uint32_t j0 = max(b * 32, js), j1 = min(b * 32 + 32, je);
+                // the block's particles: one coalesced load, then broadcast lane by lane
+                const uint32_t jl = min(b * 32 + lane, (uint32_t)(n - 1));
+                const V4 ql = rel[jl];
+                T vlx, vly, vlz;
                 if (kAbsolute) {
-                    dx += ix;
-                    dy += iy;
-                    dz += iz;
-                }
-                const T r2 = dx * dx + dy * dy + dz * dz;
-                const bool in = valid && r2 < rc2 && r2 > T(0);
-                if (!__any_sync(0xffffffffu, in)) continue;
-                T h, hr;
-                pair_jac(r2, eps2, inv_rs, gp, h, hr);
-                T w0, w1, w2;
-                if (kAbsolute) {
-                    w0 = (T)(vs[j] - vix);
-                    w1 = (T)(vs[n + j] - viy);
-                    w2 = (T)(vs[2 * n + j] - viz);
+                    vlx = (T)vs[jl];
+                    vly = (T)vs[n + jl];
+                    vlz = (T)vs[2 * n + jl];
                 } else {
-                    const float4 vj = vf[j];
-                    w0 = (T)((double)vj.x - vix);
-                    w1 = (T)((double)vj.y - viy);
-                    w2 = (T)((double)vj.z - viz);
+                    const float4 t4 = vf[jl];
+                    vlx = (T)t4.x;
+                    vly = (T)t4.y;
+                    vlz = (T)t4.z;
                 }
-                const T dw = dx * w0 + dy * w1 + dz * w2;
-                const T c = in ? hr * dw : T(0);
-                const T hh = in ? h : T(0);
-                ox += hh * w0 + c * dx;
-                oy += hh * w1 + c * dy;
-                oz += hh * w2 + c * dz;
+                for (uint32_t j = j0; j < j1; ++j) {
+                    const int src = (int)(j - b * 32);
+                    T dx = __shfl_sync(0xffffffffu, (T)ql.x, src) - xs;
+                    T dy = __shfl_sync(0xffffffffu, (T)ql.y, src) - ys;
+                    T dz = __shfl_sync(0xffffffffu, (T)ql.z, src) - zs;
+                    if (kAbsolute) {
+                        dx += ix;
+                        dy += iy;
+                        dz += iz;
+                    }
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    const bool in = valid && (all_in || r2 < rc2) && r2 > T(0);
+                    const T w0 = __shfl_sync(0xffffffffu, vlx, src) - vix;
+                    const T w1 = __shfl_sync(0xffffffffu, vly, src) - viy;
+                    const T w2 = __shfl_sync(0xffffffffu, vlz, src) - viz;
+                    if (!all_in && !__any_sync(0xffffffffu, in)) continue;
+                    T h, hr;
+                    pair_jac(r2, eps2, inv_rs, gp, h, hr);
+                    const T dw = dx * w0 + dy * w1 + dz * w2;
+                    const T c = in ? hr * dw : T(0);
+                    const T hh = in ? h : T(0);
+                    ox += hh * w0 + c * dx;
+                    oy += hh * w1 + c * dy;
+                    oz += hh * w2 + c * dz;
+                }
             }
             o[0] += (double)ox;
             o[1] += (double)oy;
@@ -394,10 +425,13 @@ cudaError_t vjp_pairs(p3m_ctx *c, const double *v_slots, double *out_slots)
     if (per_sm < 1) per_sm = 1;
     e = cudaMemsetAsync(c->counters + 3, 0, sizeof(uint32_t), c->stream);
     if (e != cudaSuccess) return e;
+    const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
+    const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
     c->launches += 1;
     k_pairs_vjp<T><<<c->num_sms * per_sm, 32, 0, c->stream>>>(
-        (const typename V4Of<T>::type *)c->rel, c->adj_vf, v_slots, c->cell_start, c->work,
-        c->work_off + c->g.n_cells, c->g, gp, c->counters + 3, out_slots);
+        (const typename V4Of<T>::type *)c->rel, c->pos, c->block_box, c->adj_vf, v_slots,
+        c->cell_start, c->work, c->work_order, c->work_off + c->g.n_cells, c->g, gp,
+        (float)(rcull * rcull), rin > 0.0 ? (float)(rin * rin) : 0.0f, c->counters + 3, out_slots);
     return cudaGetLastError();
 }
 

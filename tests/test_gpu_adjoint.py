@@ -92,7 +92,7 @@ def test_run_gradient_matches_oracle_and_finite_differences(mod):
     g = psi_t.grad.cpu().numpy()
     p = O.Params(CASE["box"], q.shape[1], CASE["mesh"], softening=CASE["soft"])
     rl, rg = O.run_gradient(psi, q, a, target, p)
-    assert abs(float(loss) - rl) < 1e-10 * rl
+    assert abs(float(loss.detach()) - rl) < 1e-10 * rl
     assert rel_rms(g, rg) < 1e-8
     eps = 1e-7 * CASE["box"] / CASE["n_p"]
     with torch.no_grad():
