@@ -150,6 +150,22 @@ def oracle_step_time(pos, mom, n_sample, seed):
     return total, O.oracle_threads(), desc
 
 
+# ---------------------------------------------------------------- replicas across ranks
+
+
+def aggregate_ranks(dist, ms_local: float, units_per_rank: int, steps: int, device=None):
+    """Whole-job rate of independent replicas (weak scaling, no data-path collective): the
+    slowest rank's time over all ranks' units.  Returns (value per second, max ms)."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return units_per_rank * world * steps / (ms_max / 1e3), ms_max
+
+
 # ---------------------------------------------------------------- our arm
 
 
@@ -212,11 +228,7 @@ def run_ours(args, rank, world, local_rank, dist):
     sim.set_timing(False)
     d1 = sim.diagnostics()
 
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n * world * args.steps / (ms_max / 1e3)
+    value, ms_max = aggregate_ranks(dist, ms_total, n, args.steps, device=dev)
 
     # ---- kernels and roofline (per launch = per step)
     K = args.steps

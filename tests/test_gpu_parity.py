@@ -274,3 +274,25 @@ def test_full_size_512_sampled(P3M):
     pos, mom = S.zeldovich(512, 1000.0, 0.5, 1513)
     err, _ = _sampled(P3M, pos, mom, 1000.0, 512, 200, 32, 0.5)
     assert err <= TOL["mixed"], err
+
+
+def test_lcdm_steps_match_oracle(P3M):
+    """Omega_m = 0.3, Omega_Lambda = 0.7 (Ch. Parameters, cosmological parameters): the kick and
+    drift factors come from quadrature; 5 steps a = 0.1 -> 0.3 in FP64 mode."""
+    pos, mom, kw = _case("eds32")
+    n = pos.shape[1]
+    a_s = S.log_spaced_steps(0.1, 0.3, 5)
+    with P3M(kw["box"], n, kw["mesh"], precision="fp64", omega_m=0.3, omega_lambda=0.7) as sim:
+        sim.set_particles(pos, mom, a=a_s[0])
+        for i in range(5):
+            sim.step(a_s[i], a_s[i + 1] - a_s[i])
+        gpos, gmom = sim.get_particles()
+    p = O.Params(kw["box"], n, kw["mesh"], softening=0.02, omega_m=0.3, omega_lambda=0.7)
+    x, m = O.wrap(pos, kw["box"]), mom.copy()
+    acc = O.accel(x, p)
+    for i in range(5):
+        x, m, acc = O.step(x, m, acc, a_s[i], a_s[i + 1] - a_s[i], p)
+    dx = gpos - x
+    dx -= kw["box"] * np.round(dx / kw["box"])
+    assert np.max(np.abs(dx)) <= 1e-11 * kw["box"]
+    assert np.max(np.abs(gmom - m)) <= 1e-9 * np.max(np.abs(m))
