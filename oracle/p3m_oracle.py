@@ -686,3 +686,129 @@ def run_gradient(psi, q, a_list, target, p: Params, mass: float = 1.0):
         lam_p = lam_p + (D[k] / mass) * lam_x
     lam_x = lam_x + mass * K1[0] * accel_vjp(xs[0], lam_p, p)
     return loss, lam_x + mass * math.sqrt(a_list[0]) * lam_p
+
+
+# --------------------------------------------------------------------------- energies
+# Readings (the guide names no energy diagnostic; its SURVEY-listed Layzer-Irvine check):
+#   comoving potential Phi with nabla^2 Phi = 4 pi G (rho - rho_bar), acceleration -grad Phi;
+#   peculiar potential energy W = (1/(2a)) sum_i m Phi(x_i) (self-interaction at r = 0
+#   excluded), kinetic energy K = sum_i |p_i|^2 / (2 m a^2);
+#   Layzer-Irvine (cosmic energy) equation d[a (K + W)]/da = -K.
+# P3M potential of particle i:
+#   Phi_i = Phi_LR(x_i) - S_i + (phi_per - phi_iso) + phi_SR,i + 4 pi Gm (N/L^3) r_s^2
+#   Phi_LR   the mesh potential IFFT(G(k) FFT(rho)) interpolated by CIC;
+#   S_i      the particle's own share of it, sum_{c,c'} w_c w_c' K(n_c - n_c'), K = IFFT(G)
+#            (its CIC weights deposited, solved and interpolated back);
+#   phi_per  what that share is without a mesh: the periodic long-range potential of a unit
+#            particle at its own position, -(4 pi Gm/L^3) sum_{k != 0} exp(-k^2 r_s^2)/k^2;
+#   phi_iso  the r = 0 limit of the isolated long-range kernel -Gm erf(r/(2 r_s))/r,
+#            -Gm/(sqrt(pi) r_s): the self-interaction, excluded (the interaction with the
+#            particle's own periodic images, phi_per - phi_iso, is kept);
+#   phi_SR   the pair sum of -Gm erfc(r/(2 r_s)) / sqrt(r^2 + eps^2);
+#   the last term: the short-range potential of the neutralising background (density
+#            -N m/L^3, and erfc(r/(2 r_s))/r integrates to 4 pi r_s^2 over space).
+# With the split at alpha = 1/(2 r_s) this is the Ewald energy term by term for one particle.
+
+
+def mesh_self_potential(pos: np.ndarray, p: Params) -> np.ndarray:
+    """S_i = sum over the 8 x 8 corner pairs of the particle's CIC stencil of
+    w_c w_c' K(n_c - n_c'), K = IFFT(G): the particle's own contribution to the mesh potential
+    at its position."""
+    M = p.mesh
+    K = np.fft.irfftn(green(p), s=(M, M, M), axes=(0, 1, 2))
+    i0, f = cic_weights(pos, p)
+    corners = [(cx, cy, cz) for cx in (0, 1) for cy in (0, 1) for cz in (0, 1)]
+    w = {}
+    for c in corners:
+        w[c] = ((f[0] if c[0] else 1 - f[0]) * (f[1] if c[1] else 1 - f[1])
+                * (f[2] if c[2] else 1 - f[2]))
+    s = np.zeros(pos.shape[1])
+    for c in corners:
+        for d in corners:
+            s += w[c] * w[d] * K[(c[0] - d[0]) % M, (c[1] - d[1]) % M, (c[2] - d[2]) % M]
+    return s
+
+
+def potential(pos: np.ndarray, p: Params) -> np.ndarray:
+    """Comoving potential Phi at each particle (its own contribution removed)."""
+    M = p.mesh
+    x = wrap(pos, p.box)
+    rho = cic_deposit(x, p)
+    phi_mesh = np.fft.irfftn(green(p) * np.fft.rfftn(rho), s=(M, M, M), axes=(0, 1, 2))
+    phi = cic_gather(phi_mesh, x, p) - mesh_self_potential(x, p)
+    if not p.short_range:
+        return phi
+    kf = 2.0 * math.pi / p.box
+    nmax = int(math.ceil(6.5 / (p.r_s * kf)))
+    nn = np.arange(-nmax, nmax + 1)
+    NX, NY, NZ = np.meshgrid(nn, nn, nn, indexing="ij")
+    k2 = kf * kf * (NX * NX + NY * NY + NZ * NZ).astype(np.float64).ravel()
+    k2 = k2[k2 > 0]
+    phi_per = -(4.0 * math.pi * p.gm / p.box ** 3) * float(np.sum(np.exp(-k2 * p.r_s ** 2) / k2))
+    phi_iso = -p.gm / (math.sqrt(math.pi) * p.r_s)
+    phi = phi + (phi_per - phi_iso)
+    lib = _clib()
+    if not hasattr(lib, "_pot_set"):
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.sr_potential_cells.argtypes = [ctypes.c_int64, dp, ctypes.c_double, ctypes.c_int64,
+                                           i64p, i64p, i64p, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, dp]
+        lib._pot_set = True
+    xx = np.ascontiguousarray(x)
+    q = Params(p.box, p.n, p.mesh, p.r_s_cells, p.cutoff, p.softening, p.deconvolve, 0, True,
+               p.omega_m, p.omega_lambda)
+    cell, _ = cell_keys(xx, q)
+    order = stable_order(cell).astype(np.int64)
+    starts = cell_start(cell[order], q.n_c ** 3)
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    sr = np.zeros(x.shape[1])
+    lib.sr_potential_cells(x.shape[1], _p(xx, ctypes.c_double), p.box, q.n_c,
+                           _p(cell, ctypes.c_int64), _p(order, ctypes.c_int64),
+                           _p(starts, ctypes.c_int64), p.r_s, p.r_c, p.eps, p.gm,
+                           _p(sr, ctypes.c_double))
+    background = 4.0 * math.pi * p.gm * (x.shape[1] / p.box ** 3) * p.r_s ** 2
+    return phi + sr + background
+
+
+def potential_energy(pos: np.ndarray, p: Params, a: float, mass: float = 1.0) -> float:
+    """W = (1/(2a)) sum_i m Phi(x_i)."""
+    return float(0.5 * mass * np.sum(potential(pos, p)) / a)
+
+
+def ewald_potential_energy(pos: np.ndarray, box: float, gm: float, alpha: float | None = None,
+                           nreal: int = 2, kmax: int = 6) -> float:
+    """Comoving Ewald energy (1/2) m sum_i [sum_{j != i} phi_E(x_i - x_j) + phi_self] of a
+    periodic set with a neutralising background, phi_E = -Gm [sum_n erfc(alpha s)/s
+    + (4 pi/L^3) sum_{k != 0} e^{-k^2/(4 alpha^2)} cos(k.r)/k^2 - pi/(alpha^2 L^3)], the self
+    term taking the images n != 0 and subtracting the r -> 0 limit 2 alpha / sqrt(pi)
+    (returned for m = 1 in units where Gm carries the mass)."""
+    L = box
+    if alpha is None:
+        alpha = 2.6 / L
+    n_ = pos.shape[1]
+    d0 = pos[:, None, :] - pos[:, :, None]
+    d0 = d0 - L * np.round(d0 / L)
+    offd = ~np.eye(n_, dtype=bool)
+    real = 0.0
+    rng = range(-nreal, nreal + 1)
+    for nx in rng:
+        for ny in rng:
+            for nz in rng:
+                sh = np.array([nx, ny, nz], dtype=np.float64)[:, None, None] * L
+                s = np.sqrt(np.sum((d0 + sh) ** 2, axis=0))
+                if nx == 0 and ny == 0 and nz == 0:
+                    real += np.sum(erfc(alpha * s[offd]) / s[offd])
+                else:
+                    real += np.sum(erfc(alpha * s) / s)  # includes i = j images
+    nn = np.arange(-kmax, kmax + 1)
+    NX, NY, NZ = np.meshgrid(nn, nn, nn, indexing="ij")
+    kv = (2.0 * np.pi / L) * np.stack([NX.ravel(), NY.ravel(), NZ.ravel()]).astype(np.float64)
+    k2 = np.sum(kv * kv, axis=0)
+    keep = k2 > 0
+    kv, k2 = kv[:, keep], k2[keep]
+    sk = np.exp(1j * (kv.T @ pos)).sum(axis=1)
+    recip = (4.0 * np.pi / L ** 3) * np.sum(np.exp(-k2 / (4 * alpha ** 2)) / k2 * np.abs(sk) ** 2)
+    background = -np.pi / (alpha ** 2 * L ** 3) * n_ * n_
+    self_term = -2.0 * alpha / math.sqrt(math.pi) * n_
+    return float(-0.5 * gm * (real + recip + background + self_term))

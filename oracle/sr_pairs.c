@@ -176,3 +176,37 @@ void sr_vjp_cells(int64_t n, const double *pos, const double *v, double box, int
         out[2 * n + k] = o[2];
     }
 }
+
+/*
+ * Short-range pair potential of each particle (Plummer-softened reading of the split):
+ *   phi_SR,i = -Gm sum_{j in the 27 cells, 0 < r_ij < r_c} erfc(r_ij / (2 r_s)) / sqrt(r_ij^2 + eps^2)
+ * (for eps = 0 the exact complement of the long-range potential -Gm erf(r/(2 r_s))/r).
+ */
+void sr_potential_cells(int64_t n, const double *pos, double box, int64_t n_c,
+                        const int64_t *cell_of, const int64_t *order, const int64_t *cell_start,
+                        double r_s, double r_c, double eps, double gm, double *phi)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t c = cell_of[k];
+        int64_t cx = c % n_c, cy = (c / n_c) % n_c, cz = c / (n_c * n_c);
+        double s = 0.0;
+        for (int64_t oz = -1; oz <= 1; ++oz)
+            for (int64_t oy = -1; oy <= 1; ++oy)
+                for (int64_t ox = -1; ox <= 1; ++ox) {
+                    int64_t nc = ((((cz + oz + n_c) % n_c) * n_c + (cy + oy + n_c) % n_c) * n_c +
+                                  (cx + ox + n_c) % n_c);
+                    for (int64_t t = cell_start[nc]; t < cell_start[nc + 1]; ++t) {
+                        int64_t j = order[t];
+                        if (j == k) continue;
+                        double dx = min_image(pos[j] - pos[k], box);
+                        double dy = min_image(pos[n + j] - pos[n + k], box);
+                        double dz = min_image(pos[2 * n + j] - pos[2 * n + k], box);
+                        double r2 = dx * dx + dy * dy + dz * dz;
+                        if (!(r2 < r_c * r_c) || r2 == 0.0) continue;
+                        s += erfc(0.5 * sqrt(r2) / r_s) / sqrt(r2 + eps * eps);
+                    }
+                }
+        phi[k] = -gm * s;
+    }
+}
