@@ -87,8 +87,10 @@ typedef struct {
 typedef struct {
     double momentum[3];   /* sum_i p_i (FP64, fixed reduction order)                       */
     double kinetic;       /* sum_i |p_i|^2 / (2 m a^2)                                      */
-    double potential;     /* NaN: not computed by this version                              */
-    double layzer_irvine; /* NaN: not computed by this version                              */
+    double potential;     /* W = (1/(2a)) sum_i m Phi_i while energy tracking is on
+                             (p3m_track_energy), else NaN                                   */
+    double layzer_irvine; /* while tracking: a(K + W) + int_{a0}^{a} K da - a0 (K0 + W0),
+                             the Layzer-Irvine residual (0 for exact dynamics), else NaN   */
     double a;             /* scale factor of the state                                      */
     uint64_t pairs;       /* ordered pairs inside r_c in the last force evaluation          */
     uint64_t pairs_total; /* the same, summed over every force evaluation of the context   */
@@ -200,7 +202,7 @@ int p3m_run_steps(p3m_ctx *ctx, const double *a_list, int n_steps, int use_graph
 int p3m_set_stream(p3m_ctx *ctx, void *stream);
 
 /*
- * Ensembles of independent simulations of any sizes (SURVEY "batched ensembles"): the
+ * Ensembles of independent simulations of any sizes (many small boxes stepped together): the
  * contexts advance together through the same schedule of scale factors.  With use_graph = 1
  * one step of every context is captured as parallel branches of a single CUDA graph (one per
  * step parity), so each step of the whole ensemble is one graph launch; with use_graph = 0
@@ -224,7 +226,7 @@ void p3m_ensemble_free(p3m_ensemble *ens);
 int p3m_autotune(p3m_ctx *ctx, int *sub_bits_out, double *ms_out);
 
 /*
- * Reverse-mode derivatives, for gradients through the step (SURVEY "differentiable P3M"):
+ * Reverse-mode derivatives, for gradients of a loss through the step:
  *
  * p3m_force_vjp: out3n = (dA/dx)^T v3n, the transposed Jacobian of the accelerations A at the
  *   current positions applied to the vector field v [3][n] (caller order).  The mesh part is
@@ -249,9 +251,35 @@ int p3m_axpy(p3m_ctx *ctx, double alpha, const double *x3n, double *y3n);
 int p3m_step_factors(const p3m_ctx *ctx, double a, double da, double *k1, double *dfac,
                      double *k2);
 
-/* Momentum, kinetic energy, pair count and cell statistics of the current state.
+/* Momentum, kinetic energy, pair count and cell statistics of the current state; with energy
+ * tracking on, also the potential energy and the Layzer-Irvine residual (which sort and
+ * evaluate the mesh at the current positions, so the next step re-evaluates the forces).
  * Synchronises the stream. */
 int p3m_diagnostics(p3m_ctx *ctx, p3m_diag *out);
+
+/*
+ * Energies of the current state.  The guide defines no energy diagnostic; this is the standard
+ * cosmic-energy check of cosmological N-body codes, the Layzer-Irvine equation
+ * d[a (K + W)]/da = -K for the comoving potential Phi with nabla^2 Phi = 4 pi G (rho - rho_bar):
+ *   *kinetic   = K = sum_i |p_i|^2 / (2 m a^2)
+ *   *potential = W = (1/(2a)) sum_i m Phi_i, Phi_i the potential at particle i without its
+ *     own r = 0 self-interaction (its periodic images kept):
+ *     Phi_i = Phi_mesh(x_i) - S_i + (phi_per - phi_iso) + Phi_SR,i + 4 pi Gm (N/L^3) r_s^2,
+ *     Phi_mesh the CIC-interpolated IFFT(G rho_k), S_i the particle's own share of it (its CIC
+ *     weights pushed through K = IFFT(G)), phi_per - phi_iso the exact long-range potential of
+ *     its own periodic images, Phi_SR,i = -Gm sum_{r_ij < r_c} erfc(r_ij/(2 r_s))/sqrt(r_ij^2 +
+ *     eps^2), and the last term the short-range potential of the neutralising background.
+ *     Pure PM (short_range = 0): Phi_mesh - S_i only.
+ * Sorts and evaluates the mesh at the current positions (with P3M the next p3m_step
+ * re-evaluates the forces).  Host pointers; synchronises.
+ *
+ * p3m_track_energy(ctx, 1) records a0 and a0 (K0 + W0) of the current state and from then on
+ * adds the trapezoid rule's share of int K da after every step (p3m_step, p3m_run_steps,
+ * graph-replayed or not; one extra reduction per step); p3m_diagnostics then reports the
+ * residual.  p3m_track_energy(ctx, 0) stops it.
+ */
+int p3m_energy(p3m_ctx *ctx, double *kinetic, double *potential);
+int p3m_track_energy(p3m_ctx *ctx, int enable);
 
 /*
  * Sorted views of the last sort (after p3m_forces / p3m_step), for checking:

@@ -20,7 +20,7 @@ written in the order the force evaluation runs:
   8. short-range pair sum over the 27 neighbouring chaining cells (plain C, ``sr_pairs.c``)
   9. comoving kick-drift-kick leapfrog
 
-Readings where the guide is silent (all listed in the design doc):
+Readings where the guide is silent:
   * split convention g(x) = erfc(x/2) + x/sqrt(pi) exp(-x^2/4), x = r/r_s, with the
     long-range filter exp(-k^2 r_s^2): the only one under which the guide's "cutoff >= 4.8
     leaves < 1 % of the force out" holds (g(4.8) = 0.92 %);
@@ -689,7 +689,7 @@ def run_gradient(psi, q, a_list, target, p: Params, mass: float = 1.0):
 
 
 # --------------------------------------------------------------------------- energies
-# Readings (the guide names no energy diagnostic; its SURVEY-listed Layzer-Irvine check):
+# Readings (the guide defines no energy diagnostic; this is the standard cosmic-energy check):
 #   comoving potential Phi with nabla^2 Phi = 4 pi G (rho - rho_bar), acceleration -grad Phi;
 #   peculiar potential energy W = (1/(2a)) sum_i m Phi(x_i) (self-interaction at r = 0
 #   excluded), kinetic energy K = sum_i |p_i|^2 / (2 m a^2);

@@ -223,11 +223,23 @@ class P3M:
         self._check(self._lib.p3m_autotune(self._ctx, ctypes.byref(b), ms.ctypes.data))
         return b.value, ms
 
+    def energy(self):
+        """(K, W): kinetic and peculiar potential energy of the current state."""
+        k, w = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.p3m_energy(self._ctx, ctypes.byref(k), ctypes.byref(w)))
+        return k.value, w.value
+
+    def track_energy(self, enable: bool = True):
+        """Starts (or stops) the Layzer-Irvine bookkeeping: diagnostics() then reports the
+        potential energy and the residual a(K + W) + int K da - a0 (K0 + W0)."""
+        self._check(self._lib.p3m_track_energy(self._ctx, 1 if enable else 0))
+
     # ------------------------------------------------------------------ introspection
     def diagnostics(self) -> dict:
         d = Diag()
         self._check(self._lib.p3m_diagnostics(self._ctx, ctypes.byref(d)))
         return {"momentum": np.array(d.momentum[:]), "kinetic": d.kinetic, "a": d.a,
+                "potential": d.potential, "layzer_irvine": d.layzer_irvine,
                 "pairs": int(d.pairs), "pairs_total": int(d.pairs_total),
                 "launches": int(d.launches), "pair_warp_j": [int(v) for v in d.pair_warp_j],
                 "pair_blocks_culled": int(d.pair_blocks_culled),

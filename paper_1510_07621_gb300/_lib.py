@@ -63,6 +63,8 @@ SIGNATURES = {
                                       _c.POINTER(_c.c_double)]),
     "p3m_get_particles": (_c.c_int, [_vp, _dp, _dp, _dp, _c.c_int]),
     "p3m_diagnostics": (_c.c_int, [_vp, _c.POINTER(Diag)]),
+    "p3m_energy": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)]),
+    "p3m_track_energy": (_c.c_int, [_vp, _c.c_int]),
     "p3m_get_cells": (_c.c_int, [_vp, _vp, _vp, _vp, _c.c_int]),
     "p3m_get_mesh": (_c.c_int, [_vp, _c.c_int, _vp, _c.c_int]),
     "p3m_get_geometry": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),

@@ -13,6 +13,8 @@
 #include <cufft.h>
 #include <math.h>
 
+#include <vector>
+
 #include "p3m_internal.cuh"
 
 namespace {
@@ -382,6 +384,244 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// ------------------------------------------------------------------ potential energy
+
+// phi_k = G(k) rho_k (the potential spectrum of the forward pass, no gradient).
+template <typename T, typename C2>
+__global__ void k_kspace_potential(const C2 *__restrict__ rk, const T *__restrict__ tk,
+                                   const T *__restrict__ tg, int M, T gconst, int green_only,
+                                   C2 *__restrict__ out)
+{
+    const int nz = M / 2 + 1;
+    const size_t total = (size_t)M * M * nz;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int iz = (int)(idx % nz);
+        const size_t t = idx / nz;
+        const int iy = (int)(t % M), ix = (int)(t / M);
+        const T kx = tk[ix], ky = tk[iy], kz = tk[iz];
+        const T k2 = kx * kx + ky * ky + kz * kz;
+        const T G = idx == 0 ? T(0) : gconst * (tg[ix] * tg[iy] * tg[iz]) / k2;
+        C2 o;
+        if (green_only) {  // the kernel K = IFFT(G) itself
+            o.x = G;
+            o.y = T(0);
+        } else {
+            const C2 r = rk[idx];
+            o.x = G * r.x;
+            o.y = G * r.y;
+        }
+        out[idx] = o;
+    }
+}
+
+// Per particle: Phi_LR(x_k) - S_k, S_k = sum_{c,c'} w_c w_c' K(n_c - n_c') (kself: K at the
+// 27 offsets {-1,0,1}^3, index (dx+1)*9 + (dy+1)*3 + (dz+1)); phi_out[k] = that + cst.
+template <typename T>
+__global__ void k_gather_potential(const double *__restrict__ pos, P3MGeom g,
+                                   const T *__restrict__ phi_mesh, const double *__restrict__ kself,
+                                   double cst, double *__restrict__ phi_out)
+{
+    const int M = g.mesh;
+    const int64_t n = g.n;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int i3[3];
+        double f3[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) stencil64(pos[d * n + k], g.inv_h, i3[d], f3[d]);
+        double w[8];
+        double phi = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int a = c >> 2, b = (c >> 1) & 1, e = c & 1;
+            w[c] = (a ? f3[0] : 1.0 - f3[0]) * (b ? f3[1] : 1.0 - f3[1]) * (e ? f3[2] : 1.0 - f3[2]);
+            const size_t node = ((size_t)wrap_index(i3[0] + a, M) * M + wrap_index(i3[1] + b, M)) * M +
+                                wrap_index(i3[2] + e, M);
+            phi += w[c] * (double)phi_mesh[node];
+        }
+        double self = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int dx = (c >> 2) - (d >> 2), dy = ((c >> 1) & 1) - ((d >> 1) & 1),
+                          dz = (c & 1) - (d & 1);
+                self += w[c] * w[d] * kself[(dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)];
+            }
+        phi_out[k] = phi - self + cst;
+    }
+}
+
+// Short-range pair potential: phi_out[k] += -Gm sum_j erfc(r/(2 r_s)) / sqrt(r^2 + eps^2),
+// the pair kernel's traversal (work items, block culling, shuffled j blocks).
+template <typename T>
+__global__ void __launch_bounds__(32)
+    k_pairs_potential(const typename V4Of<T>::type *__restrict__ rel, const double *__restrict__ pos,
+                      const float4 *__restrict__ block_box, const uint32_t *__restrict__ cell_start,
+                      const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
+                      const uint32_t *__restrict__ n_work_ptr, P3MGeom g, float rcull2,
+                      uint32_t *__restrict__ cursor, double *__restrict__ phi_out)
+{
+    using V4 = typename V4Of<T>::type;
+    constexpr bool kAbsolute = sizeof(T) == 8;
+    const int lane = threadIdx.x;
+    const int64_t n = g.n;
+    const uint32_t n_work = *n_work_ptr;
+    const T rc2 = (T)(g.r_c * g.r_c), eps2 = (T)(g.eps * g.eps), half_inv_rs = (T)(0.5 / g.r_s);
+    const int nc = g.n_c;
+    for (;;) {
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(cursor, 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= n_work) break;
+        const uint32_t item = order[slot];
+        const uint32_t cell = work[2 * (size_t)item], first = work[2 * (size_t)item + 1];
+        const uint32_t cend = cell_start[cell + 1];
+        const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
+        const uint32_t i = first + lane;
+        const bool valid = i < cend;
+        const uint32_t ii = valid ? i : first;
+        const V4 xi = rel[ii];
+        const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];
+        double acc = 0.0;
+        for (int nb = 0; nb < 27; ++nb) {
+            const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
+            const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
+            const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
+            const uint32_t js = cell_start[q], je = cell_start[q + 1];
+            if (js == je) continue;
+            const double L = g.box, cs = g.cs;
+            const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+            const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+            const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            T xs, ys, zs, ix = 0, iy = 0, iz = 0;
+            if (kAbsolute) {
+                xs = (T)xi.x;
+                ys = (T)xi.y;
+                zs = (T)xi.z;
+                ix = (T)imx;
+                iy = (T)imy;
+                iz = (T)imz;
+            } else {
+                xs = (T)((double)xi.x - (((double)wx * cs + imx) - (double)cx * cs));
+                ys = (T)((double)xi.y - (((double)wy * cs + imy) - (double)cy * cs));
+                zs = (T)((double)xi.z - (((double)wz * cs + imz) - (double)cz * cs));
+            }
+            const float cxs = (float)(xa - imx), cys = (float)(ya - imy), czs = (float)(za - imz);
+            T s = 0;
+            for (uint32_t b = js >> 5; b * 32u < je; ++b) {
+                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
+                const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
+                const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
+                if (!__any_sync(0xffffffffu, valid && ex * ex + ey * ey + ez * ez < rcull2)) continue;
+                const uint32_t j0 = max(b * 32, js), j1 = min(b * 32 + 32, je);
+                const uint32_t jl = min(b * 32 + lane, (uint32_t)(n - 1));
+                const V4 ql = rel[jl];
+                for (uint32_t j = j0; j < j1; ++j) {
+                    const int src = (int)(j - b * 32);
+                    T dx = __shfl_sync(0xffffffffu, (T)ql.x, src) - xs;
+                    T dy = __shfl_sync(0xffffffffu, (T)ql.y, src) - ys;
+                    T dz = __shfl_sync(0xffffffffu, (T)ql.z, src) - zs;
+                    if (kAbsolute) {
+                        dx += ix;
+                        dy += iy;
+                        dz += iz;
+                    }
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    const bool in = valid && r2 < rc2 && r2 > T(0);
+                    if (!__any_sync(0xffffffffu, in)) continue;
+                    const T term = erfc(sqrt(r2) * half_inv_rs) / sqrt(r2 + eps2);
+                    s += in ? term : T(0);
+                }
+            }
+            acc += (double)s;
+        }
+        if (valid) phi_out[i] -= g.gm * acc;
+    }
+}
+
+// Sum of m/2 phi over particles, per-block partials then one block (fixed order).
+__global__ void __launch_bounds__(256) k_sum_vec(const double *__restrict__ x, int64_t n, double *part)
+{
+    __shared__ double s[256];
+    double a = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        a += x[k];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+template <typename T, typename C2>
+cudaError_t potential_impl(p3m_ctx *c, double cst, double *phi_slots, double *sum_dev)
+{
+    const int M = c->g.mesh;
+    const size_t nk = (size_t)M * M * (M / 2 + 1);
+    C2 *spec = (C2 *)c->frc_k;  // free after the force evaluation; FFT(rho) stays in rho_k
+    T *mesh = (T *)c->adj_u;
+    const int gk = grid_for((int64_t)nk, 256, c->num_sms);
+    c->launches += 2;
+    if (!c->kself_ready) {  // K = IFFT(G) near the origin, once per context
+        k_kspace_potential<T, C2><<<gk, 256, 0, c->stream>>>(spec, (const T *)c->tab_k,
+                                                             (const T *)c->tab_g, M,
+                                                             (T)c->green_const, 1, spec);
+        cufftResult r = sizeof(T) == 4 ? cufftExecC2R(c->plan_c2r_one, (cufftComplex *)spec, (cufftReal *)mesh)
+                                       : cufftExecZ2D(c->plan_c2r_one, (cufftDoubleComplex *)spec,
+                                                      (cufftDoubleReal *)mesh);
+        if (r != CUFFT_SUCCESS) return cudaErrorUnknown;
+        std::vector<T> host((size_t)M * M * M);
+        double k27[27];
+        cudaError_t e = cudaMemcpyAsync(host.data(), mesh, sizeof(T) * host.size(), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return e;
+        for (int t = 0; t < 27; ++t) {
+            const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+            const size_t node = ((size_t)((dx + M) % M) * M + (dy + M) % M) * M + (dz + M) % M;
+            k27[t] = (double)host[node];
+        }
+        e = cudaMemcpyAsync(c->kself, k27, sizeof(k27), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return e;
+        c->kself_ready = true;
+    }
+    // potential mesh from the current deposit (c->rho_k holds FFT(rho) after launch_deposit + R2C)
+    k_kspace_potential<T, C2><<<gk, 256, 0, c->stream>>>((const C2 *)c->rho_k, (const T *)c->tab_k,
+                                                         (const T *)c->tab_g, M, (T)c->green_const, 0,
+                                                         spec);
+    cufftResult r = sizeof(T) == 4 ? cufftExecC2R(c->plan_c2r_one, (cufftComplex *)spec, (cufftReal *)mesh)
+                                   : cufftExecZ2D(c->plan_c2r_one, (cufftDoubleComplex *)spec,
+                                                  (cufftDoubleReal *)mesh);
+    if (r != CUFFT_SUCCESS) return cudaErrorUnknown;
+    c->launches += 1;
+    k_gather_potential<T><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+        c->pos, c->g, mesh, c->kself, cst, phi_slots);
+    if (c->short_range) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_potential<T>, 32, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(c->counters + 3, 0, sizeof(uint32_t), c->stream);
+        if (e != cudaSuccess) return e;
+        const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
+        c->launches += 1;
+        k_pairs_potential<T><<<c->num_sms * (per_sm < 1 ? 1 : per_sm), 32, 0, c->stream>>>(
+            (const typename V4Of<T>::type *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
+            c->work_order, c->work_off + c->g.n_cells, c->g, (float)(rcull * rcull), c->counters + 3,
+            phi_slots);
+    }
+    c->launches += 2;
+    k_sum_vec<<<1024, 256, 0, c->stream>>>(phi_slots, c->g.n, c->red);
+    k_sum_parts<<<1, 256, 0, c->stream>>>(c->red, 1024, sum_dev);
+    return cudaGetLastError();
+}
+
 template <typename T, typename C2>
 cudaError_t vjp_mesh(p3m_ctx *c, const double *v_slots, double *out_slots)
 {
@@ -456,6 +696,12 @@ cudaError_t launch_force_vjp(p3m_ctx *c, const double *v_slots, double *out_slot
         if (e == cudaSuccess && c->short_range) e = vjp_pairs<double>(c, v_slots, out_slots);
     }
     return e;
+}
+
+cudaError_t launch_potential(p3m_ctx *c, double cst, double *phi_slots, double *sum_dev)
+{
+    return c->precision == P3M_PREC_MIXED ? potential_impl<float, cufftComplex>(c, cst, phi_slots, sum_dev)
+                                          : potential_impl<double, cufftDoubleComplex>(c, cst, phi_slots, sum_dev);
 }
 
 cudaError_t launch_density_loss(p3m_ctx *c, const double *target, double *loss_dev, double *grad_slots)

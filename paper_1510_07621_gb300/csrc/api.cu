@@ -187,7 +187,8 @@ void release(p3m_ctx *c)
                     c->tab_k,     c->tab_kg,   c->tab_g,        c->work_key, c->work_key_alt,
                     c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
                     c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac,
-                    c->adj_u,     c->adj_vf,   c->adj_vs,       c->adj_out};
+                    c->adj_u,     c->adj_vf,   c->adj_vs,       c->adj_out,  c->kself,
+                    c->li};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -310,7 +311,13 @@ int step_body(p3m_ctx *c, double a, double da, bool from_table)
         Phase ph(c, PH_KICK_DRIFT);
         CK(launch_kick_drift_keys(c, true, k1, dfac, from_table));
     }
-    return evaluate(c, k2, nullptr, from_table);
+    int rc = evaluate(c, k2, nullptr, from_table);
+    if (rc) return rc;
+    if (c->track_energy) {
+        Phase ph(c, PH_OTHER);
+        CK(launch_li_update(c, from_table ? c->cur_fac + 3 : nullptr, a + da));
+    }
+    return P3M_OK;
 }
 
 // Buffers whose roles swap during a step (all return to their roles after two steps).
@@ -500,8 +507,9 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->tab_k, real * M},   {(void **)&c->tab_kg, real * M},
             {(void **)&c->tab_g, real * M},   {(void **)&c->tab_invw2, 8 * M},
             {(void **)&c->tab_one, 8 * M},    {(void **)&c->ps_acc, 8 * (3 * (M / 2) + 1)},
-            {(void **)&c->fac_table, 8 * 3 * (size_t)P3M_MAX_GRAPH_STEPS},
+            {(void **)&c->fac_table, 8 * 4 * (size_t)P3M_MAX_GRAPH_STEPS},
             {(void **)&c->step_idx, 16},      {(void **)&c->cur_fac, 32},
+            {(void **)&c->kself, 8 * 27},     {(void **)&c->li, 8 * 4},
             {(void **)&c->adj_u, 3 * real * M3}, {(void **)&c->adj_vf, 16 * N},
             {(void **)&c->adj_vs, 24 * N},    {(void **)&c->adj_out, 24 * N},
         };
@@ -754,6 +762,10 @@ extern "C" int p3m_get_particles(p3m_ctx *c, double *pos, double *mom, double *a
     return P3M_OK;
 }
 
+namespace {
+int energy_now(p3m_ctx *c, double *kin, double *pot);
+}
+
 extern "C" int p3m_diagnostics(p3m_ctx *c, p3m_diag *out)
 {
     if (!c || !out) return fail(c, P3M_EINVAL, "p3m_diagnostics: NULL argument");
@@ -764,6 +776,14 @@ extern "C" int p3m_diagnostics(p3m_ctx *c, p3m_diag *out)
     out->n = c->g.n;
     out->n_cells_side = c->g.n_c;
     if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_diagnostics: no particles loaded");
+    if (c->track_energy) {
+        double kin = 0.0, pot = 0.0, li[4];
+        int rc = energy_now(c, &kin, &pot);
+        if (rc) return rc;
+        CK(cudaMemcpy(li, c->li, sizeof(li), cudaMemcpyDeviceToHost));
+        out->potential = pot;
+        out->layzer_irvine = c->a * (kin + pot) + li[0] - c->li_e0;
+    }
     double r[4];
     CK(launch_diag(c, r));
     out->momentum[0] = r[0];
@@ -1006,14 +1026,15 @@ extern "C" int p3m_ensemble_run(p3m_ensemble *e, const double *a_list, int n_ste
             }
     } else {
         // per-step factors of every context, and its step counter reset
-        std::vector<double> fac(3 * (size_t)n_steps);
+        std::vector<double> fac(4 * (size_t)n_steps);
         for (int i = 0; i < e->n; ++i) {
             p3m_ctx *c = e->c[i];
             for (int k = 0; k < n_steps; ++k) {
                 const double a = a_list[k], a2 = a_list[k + 1], am = a + 0.5 * (a2 - a);
-                fac[3 * k] = c->mass * p3m_kick_factor(c->cosmo, a, am);
-                fac[3 * k + 1] = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
-                fac[3 * k + 2] = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+                fac[4 * k] = c->mass * p3m_kick_factor(c->cosmo, a, am);
+                fac[4 * k + 1] = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
+                fac[4 * k + 2] = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+                fac[4 * k + 3] = a2;
             }
             cudaError_t err = cudaMemcpyAsync(c->fac_table, fac.data(), sizeof(double) * fac.size(),
                                               cudaMemcpyHostToDevice, c->stream);
@@ -1243,5 +1264,95 @@ extern "C" int p3m_density_loss(p3m_ctx *c, const double *target, double *loss, 
     }
     CK(cudaMemcpyAsync(loss, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return P3M_OK;
+}
+
+// ---------------------------------------------------------------- energies
+
+namespace {
+
+// phi_per - phi_iso: the long-range potential a particle feels from its own periodic images
+// (with the neutralising background), by the Ewald identity at alpha = 2.6/L for the lattice
+// sum and the split's alpha = 1/(2 r_s) for the short-range images:
+//   (4 pi/L^3) sum_{k != 0} exp(-k^2 r_s^2)/k^2 = psi_self - sum_{n != 0} erfc(|n|L/(2 r_s))/(|n|L)
+//                                                  + 4 pi r_s^2/L^3 + 1/(sqrt(pi) r_s),
+// psi_self the alpha-independent Ewald self term of one particle per cell.
+double image_potential(const P3MGeom &g)
+{
+    const double L = g.box, alpha = 2.6 / L, rs = g.r_s;
+    double real = 0.0, recip = 0.0, srimg = 0.0;
+    for (int x = -3; x <= 3; ++x)
+        for (int y = -3; y <= 3; ++y)
+            for (int z = -3; z <= 3; ++z) {
+                if (!x && !y && !z) continue;
+                const double r = L * sqrt((double)(x * x + y * y + z * z));
+                real += erfc(alpha * r) / r;
+                srimg += erfc(0.5 * r / rs) / r;
+            }
+    const double kf = 2.0 * M_PI / L;
+    for (int x = -8; x <= 8; ++x)
+        for (int y = -8; y <= 8; ++y)
+            for (int z = -8; z <= 8; ++z) {
+                if (!x && !y && !z) continue;
+                const double k2 = kf * kf * (double)(x * x + y * y + z * z);
+                recip += exp(-k2 / (4.0 * alpha * alpha)) / k2;
+            }
+    const double V = L * L * L;
+    const double psi_self = real + 4.0 * M_PI / V * recip - M_PI / (alpha * alpha * V) -
+                            2.0 * alpha / sqrt(M_PI);
+    const double ksum = psi_self - srimg + 4.0 * M_PI * rs * rs / V + 1.0 / (sqrt(M_PI) * rs);
+    return -g.gm * ksum + g.gm / (sqrt(M_PI) * rs);  // phi_per - phi_iso
+}
+
+int energy_now(p3m_ctx *c, double *kin, double *pot)
+{
+    int rc = key_current(c);
+    if (!rc) rc = evaluate(c, 0.0, nullptr, false, false);
+    if (rc) return rc;
+    double cst = 0.0;
+    if (c->short_range) {
+        const double V = c->g.box * c->g.box * c->g.box;
+        cst = image_potential(c->g) + 4.0 * M_PI * c->g.gm * ((double)c->g.n / V) * c->g.r_s * c->g.r_s;
+    }
+    double *sum_dev = c->red + 1024 * 4 + 5;
+    CK(launch_potential(c, cst, c->adj_out, sum_dev));
+    double sum = 0.0, r[4];
+    CK(cudaMemcpyAsync(&sum, sum_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(launch_diag(c, r));  // synchronises
+    *pot = 0.5 * c->mass * sum / c->a;
+    *kin = r[3] / (2.0 * c->mass * c->a * c->a);
+    c->forces_valid = !c->short_range;
+    return P3M_OK;
+}
+
+}  // namespace
+
+extern "C" int p3m_energy(p3m_ctx *c, double *kinetic, double *potential)
+{
+    if (!c || !kinetic || !potential) return fail(c, P3M_EINVAL, "p3m_energy: NULL argument");
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_energy: no particles loaded");
+    return energy_now(c, kinetic, potential);
+}
+
+extern "C" int p3m_track_energy(p3m_ctx *c, int enable)
+{
+    if (!c) return P3M_EINVAL;
+    if (!enable) {
+        if (c->track_energy) ++c->geom_version;
+        c->track_energy = false;
+        return P3M_OK;
+    }
+    if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_track_energy: no particles loaded");
+    double k0 = 0.0, w0 = 0.0;
+    int rc = energy_now(c, &k0, &w0);
+    if (rc) return rc;
+    double p2 = 2.0 * c->mass * c->a * c->a * k0;
+    const double li0[4] = {0.0, p2, c->a, 0.0};
+    CK(cudaMemcpyAsync(c->li, li0, sizeof(li0), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->li_a0 = c->a;
+    c->li_e0 = c->a * (k0 + w0);
+    c->track_energy = true;
+    ++c->geom_version;  // captured steps lack the tracking kernels
     return P3M_OK;
 }

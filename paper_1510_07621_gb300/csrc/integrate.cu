@@ -139,15 +139,28 @@ cudaError_t launch_kick(p3m_ctx *c, double kfac, const double *kfac_dev)
 }
 
 namespace {
-// First kernel of a graph-replayed step: the step's factors (K1, D, K2) from the table into
-// the fixed slot the other kernels read, and the step counter advanced.
+// First kernel of a graph-replayed step: the step's factors (K1, D, K2, a at the end) from the
+// table into the fixed slot the other kernels read, and the step counter advanced.
 __global__ void k_step_begin(const double *__restrict__ table, uint32_t *step_idx, double *cur)
 {
     const uint32_t s = *step_idx;
-    cur[0] = table[3 * s];
-    cur[1] = table[3 * s + 1];
-    cur[2] = table[3 * s + 2];
+    cur[0] = table[4 * s];
+    cur[1] = table[4 * s + 1];
+    cur[2] = table[4 * s + 2];
+    cur[3] = table[4 * s + 3];
     *step_idx = s + 1;
+}
+
+// Trapezoid update of the Layzer-Irvine integral of K da from sum p^2 at the step's end.
+__global__ void k_li_update(const double *__restrict__ p2, const double *__restrict__ a_dev,
+                            double a_host, double mass, double *li)
+{
+    const double a = a_dev ? *a_dev : a_host;
+    const double k_now = *p2 / (2.0 * mass * a * a);
+    const double k_prev = li[1] / (2.0 * mass * li[2] * li[2]);
+    li[0] += 0.5 * (k_prev + k_now) * (a - li[2]);
+    li[1] = *p2;
+    li[2] = a;
 }
 }  // namespace
 
@@ -171,6 +184,15 @@ cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst)
 {
     c->launches += 1;
     k_scatter<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(src, c->pid, c->g.n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_li_update(p3m_ctx *c, const double *a_now_dev, double a_now)
+{
+    c->launches += 3;
+    k_diag_partial<<<kRedBlocks, kRedThreads, 0, c->stream>>>(c->mom, c->g.n, c->red);
+    k_diag_final<<<1, kRedThreads, 0, c->stream>>>(c->red, kRedBlocks);
+    k_li_update<<<1, 1, 0, c->stream>>>(c->red + kRedBlocks * 4 + 3, a_now_dev, a_now, c->mass, c->li);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,14 @@ struct p3m_ctx {
     double *adj_vs;    // v in slot order, FP64 [3][n]
     double *adj_out;   // result in slot order [3][n]
 
+    // energies: K = IFFT(G) at the 27 offsets around the origin (mesh self-energy), the
+    // Layzer-Irvine bookkeeping [integral K da, sum p^2 at the last step, a at the last step]
+    double *kself;
+    bool kself_ready;
+    double *li;
+    bool track_energy;
+    double li_a0, li_e0;
+
     bool have_particles;
     bool forces_valid;
     bool sorted_valid;
@@ -167,6 +175,11 @@ cudaError_t launch_to_slots(p3m_ctx *c, const double *v, double *vs);
 cudaError_t launch_force_vjp(p3m_ctx *c, const double *v_slots, double *out_slots);
 // loss_dev = sum (rho/n_bar - target)^2 over the deposited mesh; grad_slots (nullable) = dL/dx
 cudaError_t launch_density_loss(p3m_ctx *c, const double *target, double *loss_dev, double *grad_slots);
+// phi_slots = potential of each particle (cst added), *sum_dev = sum over particles; needs the
+// sorted, evaluated state with FFT(rho) in rho_k
+cudaError_t launch_potential(p3m_ctx *c, double cst, double *phi_slots, double *sum_dev);
+// Layzer-Irvine: sum p^2 now, then li[0] += (K_prev + K_now)/2 (a_now - li[2]), K = sum p^2/(2 m a^2)
+cudaError_t launch_li_update(p3m_ctx *c, const double *a_now_dev, double a_now);
 
 // host helpers (api.cu)
 // Records a message for p3m_last_error(NULL) and returns code.

@@ -44,3 +44,30 @@ def test_p3m_potential_energy_matches_ewald():
         p = O.Params(L, n, mesh, cutoff=cutoff, softening=0.0)
         w = O.potential_energy(pos, p, a=1.0)
         assert abs(w - ref) < tol * abs(ref), (cutoff, mesh, w, ref)
+
+
+def test_layzer_irvine_holds_for_the_oracle_dynamics():
+    """d[a(K + W)]/da = -K along the oracle's own KDK trajectory of a quasi-linear Zel'dovich
+    start: the residual a(K+W) + int K da - a0(K0+W0) stays below 1% of a K (the mesh force
+    is not the exact gradient of the interpolated potential, so it does not vanish), while a
+    wrong sign or a missing position-dependent term of W would leave O(1) residuals."""
+    box, n_p, mesh = 24.0, 12, 24
+    pos, mom = S.zeldovich(n_p, box, 0.02, 1512)
+    n = pos.shape[1]
+    p = O.Params(box, n, mesh, softening=0.02)
+    a_s = S.log_spaced_steps(0.02, 0.06, 16)
+    x, m = O.wrap(pos, box), mom.copy()
+    acc = O.accel(x, p)
+    ks = [O.kinetic_energy(m, a_s[0])]
+    ws = [O.potential_energy(x, p, a_s[0])]
+    for i in range(16):
+        x, m, acc = O.step(x, m, acc, a_s[i], a_s[i + 1] - a_s[i], p)
+        ks.append(O.kinetic_energy(m, a_s[i + 1]))
+        ws.append(O.potential_energy(x, p, a_s[i + 1]))
+    ks, ws = np.array(ks), np.array(ws)
+    integral = float(np.sum(0.5 * (ks[1:] + ks[:-1]) * np.diff(a_s)))
+    res = a_s[-1] * (ks[-1] + ws[-1]) + integral - a_s[0] * (ks[0] + ws[0])
+    assert abs(res) < 1e-2 * a_s[-1] * ks[-1], (res, a_s[-1] * ks[-1])
+    # the same bookkeeping with W's sign flipped fails by far
+    bad = a_s[-1] * (ks[-1] - ws[-1]) + integral - a_s[0] * (ks[0] - ws[0])
+    assert abs(bad) > 0.3 * a_s[-1] * ks[-1]
