@@ -188,7 +188,7 @@ void release(p3m_ctx *c)
                     c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
                     c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac,
                     c->adj_u,     c->adj_vf,   c->adj_vs,       c->adj_out,  c->kself,
-                    c->li};
+                    c->li,        c->relx};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -415,7 +415,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         return fail(c, P3M_EINVAL, "p3m_init: unknown precision mode");
     if (!(opt.softening >= 0.0) || !isfinite(opt.softening))
         return fail(c, P3M_EINVAL, "p3m_init: softening must be >= 0");
-    if (opt.sub_bits > 3) return fail(c, P3M_EINVAL, "p3m_init: sub_bits must be in 0..3");
+    if (opt.sub_bits > 5) return fail(c, P3M_EINVAL, "p3m_init: sub_bits must be in 0..5");
     if (!finite_pos(cs.omega_m) || !(cs.omega_lambda >= 0.0) || !isfinite(cs.omega_lambda))
         return fail(c, P3M_EINVAL, "p3m_init: need omega_m > 0 and omega_lambda >= 0");
 
@@ -493,6 +493,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->pid, 4 * N},        {(void **)&c->pid_alt, 4 * N},
             {(void **)&c->rel, 4 * real * N}, {(void **)&c->keys, 4 * N},
             {(void **)&c->block_box, 32 * ((N + 31) / 32)},
+            {(void **)&c->relx, opt.precision == P3M_PREC_MIXED ? 384 * ((N + 31) / 32) : 16},
             {(void **)&c->keys_alt, 4 * N},   {(void **)&c->vals, 4 * N},
             {(void **)&c->vals_alt, 4 * N},   {(void **)&c->digit_counts, 4 * 256 * (size_t)c->n_tiles},
             {(void **)&c->scan_aux, 4 * (scan_n / P3M_SORT_TILE + 4)},

@@ -43,6 +43,7 @@ struct p3m_ctx {
     uint32_t *pid_alt;
     void *rel;  // float4 (mixed) or double4 (fp64): position relative to its cell origin
     float4 *block_box;  // per 32-slot block of the sorted order: lo, hi (FP32, absolute)
+    float *relx;        // FP32 mode: rel as block-SoA, per 32-slot block x[32] y[32] z[32]
 
     // sort
     uint32_t *keys, *keys_alt, *vals, *vals_alt;

@@ -113,23 +113,7 @@ struct GPoly {
     float c[12];
 };
 
-// g(r/r_s) (r^2 + eps^2)^-3/2 for one pair, FP32.  Only meaningful for 0 < r2 < r_c^2; the
-// caller selects 0 for every other pair (r2 = 0 gives inf/NaN here, which the select drops).
-__device__ __forceinline__ float pair_factor32(float r2, float eps2, const GPoly &gp)
-{
-    const float t = rsqrt_approx(r2);
-    const float s = rsqrt_approx(r2 + eps2);
-    const float r = r2 * t;
-    const float r3 = r2 * r;
-    const float tau = fmaf(r2, gp.c[11], -1.0f);
-    float p = gp.c[10];
-#pragma unroll
-    for (int k = 9; k >= 0; --k) p = fmaf(p, tau, gp.c[k]);
-    const float gval = fmaf(r3, p, 1.0f);
-    return gval * (s * s * s);
-}
-
-// The same in FP64, g from erfc and exp.
+// g(r/r_s) (r^2 + eps^2)^-3/2 for one pair in FP64, g from erfc and exp.
 __device__ __forceinline__ double pair_factor64(double r2, double eps2, double inv_rs)
 {
     const double s = 1.0 / sqrt(r2 + eps2);
@@ -140,11 +124,6 @@ __device__ __forceinline__ double pair_factor64(double r2, double eps2, double i
 
 template <typename T>
 __device__ __forceinline__ T pair_factor(T r2, T eps2, const GPoly &gp, double inv_rs);
-template <>
-__device__ __forceinline__ float pair_factor<float>(float r2, float eps2, const GPoly &gp, double)
-{
-    return pair_factor32(r2, eps2, gp);
-}
 template <>
 __device__ __forceinline__ double pair_factor<double>(double r2, double eps2, const GPoly &,
                                                       double inv_rs)
@@ -213,6 +192,7 @@ __global__ void __launch_bounds__(32)
             Neighbour q;
             q.start = cell_start[nb];
             q.end = cell_start[nb + 1];
+            if (q.start == q.end) q.start = q.end = 0;  // empty: the tile walk skips it
             const double L = g.box, cs = g.cs;
             q.imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
             q.imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
@@ -391,6 +371,356 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// ------------------------------------------------------------------ FP32 mode, packed lanes
+// The FP32 kernel proper.  Same traversal as k_pairs (one-warp CTAs, work items of one cell's
+// particles, 27 neighbour cells streamed through two bulk-copy buffers, block culling and the
+// all-inside fast path), but every lane evaluates two j particles at once with the packed
+// f32x2 arithmetic of sm_100-class GPUs: one instruction issues both halves, so the FP32 pipe
+// rather than instruction issue bounds the loop.  The j coordinates come from the block-SoA
+// copy relx (per 32-slot block x[32] y[32] z[32]), so the pair (j, j+1), j even, is one
+// 8-byte shared-memory load per coordinate.
+//
+// r^2 starts its sum at kTiny = 1e-20: a pair at r = 0 (the particle itself, or a coincident
+// one) then gets a finite factor, and its contribution f * d is exactly 0 without a select;
+// for r^2 > 1e-12 the addend is absorbed by FP32 rounding.  Pairs are counted when
+// kTiny < r^2 < r_c^2.
+
+typedef unsigned long long f2;
+
+// A neighbour cell for the FP32 kernel: its shift as an FP32 value plus the FP32 residual of
+// the FP64 shift (the pair (sx, rx) carries the FP64 value to ~2^-48), and its periodic image.
+struct NeighbourF {
+    uint32_t start, end;
+    float sx, sy, sz, rx, ry, rz;
+    float imx, imy, imz, pad;
+};
+
+// s + c += x, Knuth's TwoSum: the FP32 sum s and the running compensation c keep the rounding
+// error of every addition, so the per-tile partial sums add up as accurately as in FP64
+// without touching the (slow) FP64 pipe inside the tile loop.
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += e;
+}
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+constexpr float kTiny = 1e-20f;
+
+// Per-lane constants of the packed evaluation.
+struct PairConst2 {
+    f2 c[11];    // polynomial coefficients, both halves equal
+    f2 c11, m1, one, eps2, tiny;
+};
+
+// The factor g(r/r_s) (r^2 + eps^2)^-3/2 of both halves of r2 (r2 includes kTiny).
+__device__ __forceinline__ f2 pair_factor2(f2 r2, const PairConst2 &k)
+{
+    float r2l, r2h, s2l, s2h;
+    const f2 s2 = f2_add(r2, k.eps2);
+    f2_unpack(r2, r2l, r2h);
+    f2_unpack(s2, s2l, s2h);
+    const f2 t = f2_pack(rsqrt_approx(r2l), rsqrt_approx(r2h));
+    const f2 s = f2_pack(rsqrt_approx(s2l), rsqrt_approx(s2h));
+    const f2 r3 = f2_mul(r2, f2_mul(r2, t));
+    const f2 tau = f2_fma(r2, k.c11, k.m1);
+    f2 p = k.c[10];
+#pragma unroll
+    for (int q = 9; q >= 0; --q) p = f2_fma(p, tau, k.c[q]);
+    const f2 gval = f2_fma(r3, p, k.one);
+    return f2_mul(gval, f2_mul(f2_mul(s, s), s));
+}
+
+__global__ void __launch_bounds__(32)
+    k_pairs_x2(const float *__restrict__ relx, const float4 *__restrict__ rel,
+               const double *__restrict__ pos, const float4 *__restrict__ block_box,
+               const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ work,
+               const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_work_ptr,
+               P3MGeom g, GPoly gp, float rcull2, float rin2, const double *__restrict__ acc_in,
+               double *__restrict__ acc_out, double *__restrict__ mom, double kfac,
+               const double *__restrict__ kfac_dev, uint32_t *__restrict__ counters,
+               unsigned long long *__restrict__ pair_count)
+{
+    constexpr int kBlockFloats = 96;  // x[32] y[32] z[32]
+    if (kfac_dev) kfac = *kfac_dev;
+    __shared__ __align__(128) float sj[2][kBlocksPerTile * kBlockFloats];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ NeighbourF nbr[27];
+
+    const int lane = threadIdx.x;
+    const int64_t n = g.n;
+    const int64_t nblocks = (n + 31) >> 5;
+    const uint32_t n_work = *n_work_ptr;
+    const float rc2 = (float)(g.r_c * g.r_c);
+    const int nc = g.n_c;
+    PairConst2 kc;
+#pragma unroll
+    for (int q = 0; q < 11; ++q) kc.c[q] = f2_pack(gp.c[q], gp.c[q]);
+    kc.c11 = f2_pack(gp.c[11], gp.c[11]);
+    kc.m1 = f2_pack(-1.0f, -1.0f);
+    kc.one = f2_pack(1.0f, 1.0f);
+    const float eps2 = (float)(g.eps * g.eps);
+    kc.eps2 = f2_pack(eps2, eps2);
+    kc.tiny = f2_pack(kTiny, kTiny);
+
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0u;
+    unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0, st_culled = 0,
+                       st_tiles = 0, st_empty_tiles = 0;
+    bool timed_out = false;
+
+    for (;;) {
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(&counters[0], 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= n_work) break;
+        const uint32_t item = order[slot];
+        const uint32_t cell = work[2 * (size_t)item];
+        const uint32_t first = work[2 * (size_t)item + 1];
+        const uint32_t cend = cell_start[cell + 1];
+        const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
+        if (lane < 27) {
+            const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+            const int ux = cx + ox, uy = cy + oy, uz = cz + oz;
+            const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
+            const uint32_t nb = ((uint32_t)wz * nc + wy) * nc + wx;
+            NeighbourF q;
+            q.start = cell_start[nb];
+            q.end = cell_start[nb + 1];
+            if (q.start == q.end) q.start = q.end = 0;  // empty: the tile walk skips it
+            const double L = g.box, cs = g.cs;
+            const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+            const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+            const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            const double sx = ((double)wx * cs + imx) - (double)cx * cs;
+            const double sy = ((double)wy * cs + imy) - (double)cy * cs;
+            const double sz = ((double)wz * cs + imz) - (double)cz * cs;
+            q.sx = (float)sx;
+            q.sy = (float)sy;
+            q.sz = (float)sz;
+            q.rx = (float)(sx - (double)q.sx);
+            q.ry = (float)(sy - (double)q.sy);
+            q.rz = (float)(sz - (double)q.sz);
+            q.imx = (float)imx;
+            q.imy = (float)imy;
+            q.imz = (float)imz;
+            q.pad = 0.0f;
+            nbr[lane] = q;
+        }
+        __syncwarp();
+
+        const uint32_t i = first + lane;
+        const bool valid = i < cend;
+        const uint32_t ii = valid ? i : first;
+        const float4 xi = rel[ii];
+        // absolute position in FP32, for the bounding-box tests only (their margins cover
+        // the FP32 rounding of coordinates up to the box size)
+        const float xa = (float)pos[ii], ya = (float)pos[n + ii], za = (float)pos[2 * n + ii];
+        float sax = 0.0f, say = 0.0f, saz = 0.0f, cax = 0.0f, cay = 0.0f, caz = 0.0f;
+
+        auto next_tile = [&](int &nb, uint32_t &b) {
+            while (nb < 27 && b * 32u >= nbr[nb].end) {
+                ++nb;
+                if (nb < 27) b = nbr[nb].start >> 5;
+            }
+        };
+        auto issue = [&](int nb, uint32_t b, int to) {
+            const uint32_t bend = min(b + kBlocksPerTile, (nbr[nb].end + 31) >> 5);
+            const uint32_t bytes = (bend - b) * (uint32_t)(kBlockFloats * sizeof(float));
+            mbar_expect_tx(&bar[to], bytes);
+            bulk_load(&sj[to][0], relx + (size_t)b * kBlockFloats, bytes, &bar[to]);
+        };
+
+        int nb_c = 0;
+        uint32_t b_c = nbr[0].start >> 5;
+        next_tile(nb_c, b_c);
+        int buf = 0;
+        if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
+        while (nb_c < 27) {
+            const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
+            const uint32_t bend = min(b_c + kBlocksPerTile, (nend + 31) >> 5);
+            int nb_n = nb_c;
+            uint32_t b_n = bend;
+            next_tile(nb_n, b_n);
+            __syncwarp();
+            if (nb_n < 27 && lane == 0) issue(nb_n, b_n, buf ^ 1);
+            const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+            parity ^= 1u << buf;
+            if (__any_sync(0xffffffffu, !ok)) {
+                timed_out = true;
+                if (nb_n < 27) mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
+                break;
+            }
+            const NeighbourF &q = nbr[nb_c];
+            // x_i in the neighbour cell's frame: (x_i - s) with s = sx + rx
+            const float xs = (xi.x - q.sx) - q.rx;
+            const float ys = (xi.y - q.sy) - q.ry;
+            const float zs = (xi.z - q.sz) - q.rz;
+            const f2 xs2 = f2_pack(xs, xs), ys2 = f2_pack(ys, ys), zs2 = f2_pack(zs, zs);
+            const float cxs = xa - q.imx, cys = ya - q.imy, czs = za - q.imz;
+            f2 px = 0, py = 0, pz = 0;  // bit pattern 0 = (+0.0f, +0.0f)
+            uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0, n_culled = 0;
+
+            // one aligned pair (p, p+1) of the block at bx; lo/hi: which halves take part
+            auto pair_tested = [&](const float *bx, uint32_t p, bool lo, bool hi) {
+                const f2 dx = f2_sub(*(const f2 *)(bx + p), xs2);
+                const f2 dy = f2_sub(*(const f2 *)(bx + 32 + p), ys2);
+                const f2 dz = f2_sub(*(const f2 *)(bx + 64 + p), zs2);
+                const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, kc.tiny)));
+                float r2l, r2h;
+                f2_unpack(r2, r2l, r2h);
+                const bool inl = lo && r2l < rc2, inh = hi && r2h < rc2;
+                if (!__any_sync(0xffffffffu, inl || inh)) return;
+                ++n_eval;
+                float fl, fh;
+                f2_unpack(pair_factor2(r2, kc), fl, fh);
+                const f2 f = f2_pack(inl ? fl : 0.0f, inh ? fh : 0.0f);
+                px = f2_fma(f, dx, px);
+                py = f2_fma(f, dy, py);
+                pz = f2_fma(f, dz, pz);
+                cnt += (inl && r2l > kTiny) + (inh && r2h > kTiny);
+            };
+
+            for (uint32_t b = b_c; b < bend; ++b) {
+                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
+                const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
+                const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
+                const bool near = valid && ex * ex + ey * ey + ez * ez < rcull2;
+                if (!__any_sync(0xffffffffu, near)) {
+                    ++n_culled;
+                    continue;
+                }
+                const uint32_t j0 = max(b * 32, nstart) - b * 32;  // block-relative range
+                const uint32_t j1 = min(b * 32 + 32, nend) - b * 32;
+                const float *bx = sj[buf] + (b - b_c) * kBlockFloats;
+                const float fx = fmaxf(cxs - lo.x, hi.x - cxs);
+                const float fy = fmaxf(cys - lo.y, hi.y - cys);
+                const float fz = fmaxf(czs - lo.z, hi.z - czs);
+                uint32_t p = j0 & ~1u;
+                if (__all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2)) {
+                    // the block lies within r_c of every particle of the warp
+                    n_fast += j1 - j0;
+                    if ((j0 & 1u) && j0 < j1) {
+                        pair_tested(bx, p, false, true);
+                        p += 2;
+                    }
+#pragma unroll 2
+                    for (; p + 1 < j1; p += 2) {
+                        const f2 dx = f2_sub(*(const f2 *)(bx + p), xs2);
+                        const f2 dy = f2_sub(*(const f2 *)(bx + 32 + p), ys2);
+                        const f2 dz = f2_sub(*(const f2 *)(bx + 64 + p), zs2);
+                        const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, kc.tiny)));
+                        const f2 f = pair_factor2(r2, kc);
+                        px = f2_fma(f, dx, px);
+                        py = f2_fma(f, dy, py);
+                        pz = f2_fma(f, dz, pz);
+                        float r2l, r2h;
+                        f2_unpack(r2, r2l, r2h);
+                        cnt += (r2l > kTiny) + (r2h > kTiny);
+                    }
+                    if (p < j1) pair_tested(bx, p, true, false);
+                    continue;
+                }
+                n_tested += j1 - j0;
+                if ((j0 & 1u) && j0 < j1) {
+                    pair_tested(bx, p, false, true);
+                    p += 2;
+                }
+                for (; p + 1 < j1; p += 2) pair_tested(bx, p, true, true);
+                if (p < j1) pair_tested(bx, p, true, false);
+            }
+            float lo_, hi_;
+            f2_unpack(px, lo_, hi_);
+            two_sum_add(sax, cax, lo_ + hi_);
+            f2_unpack(py, lo_, hi_);
+            two_sum_add(say, cay, lo_ + hi_);
+            f2_unpack(pz, lo_, hi_);
+            two_sum_add(saz, caz, lo_ + hi_);
+            if (valid) my_pairs += cnt;
+            st_fast += n_fast;
+            st_tested += n_tested;
+            st_eval += n_eval;
+            st_culled += n_culled;
+            ++st_tiles;
+            if (n_culled == bend - b_c) ++st_empty_tiles;
+            buf ^= 1;
+            nb_c = nb_n;
+            b_c = b_n;
+        }
+        if (timed_out) break;
+        if (valid) {
+            const double a3[3] = {g.gm * ((double)sax + (double)cax), g.gm * ((double)say + (double)cay),
+                                  g.gm * ((double)saz + (double)caz)};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double tot = (acc_in ? acc_in[d * n + i] : 0.0) + a3[d];
+                acc_out[d * n + i] = tot;
+                if (kfac != 0.0) mom[d * n + i] = __dadd_rn(mom[d * n + i], __dmul_rn(kfac, tot));
+            }
+        }
+        __syncwarp();
+    }
+    (void)nblocks;
+    if (timed_out && lane == 0) atomicOr(&counters[1], P3M_FLAG_TIMEOUT);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+    if (lane == 0) {
+        if (my_pairs) {
+            atomicAdd(pair_count, my_pairs);
+            atomicAdd(pair_count + 1, my_pairs);
+        }
+        if (st_fast) atomicAdd(pair_count + 2, st_fast);
+        if (st_tested) atomicAdd(pair_count + 3, st_tested);
+        if (st_eval) atomicAdd(pair_count + 4, 2 * st_eval);
+        if (st_culled) atomicAdd(pair_count + 5, st_culled);
+        if (st_tiles) atomicAdd(pair_count + 6, st_tiles);
+        if (st_empty_tiles) atomicAdd(pair_count + 7, st_empty_tiles);
+    }
+}
+
 template <typename T>
 cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
                        const double *kfac_dev)
@@ -417,11 +747,33 @@ cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double
     return cudaGetLastError();
 }
 
+cudaError_t pairs_x2_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+                          const double *kfac_dev)
+{
+    cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
+    cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2, 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    GPoly gp;
+    for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
+    const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
+    const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
+    c->launches += 1;
+    k_pairs_x2<<<c->num_sms * per_sm, 32, 0, c->stream>>>(
+        c->relx, (const float4 *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
+        c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
+        rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, kfac_dev,
+        c->counters, c->pair_count);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
                          const double *kfac_dev)
 {
-    return c->precision == P3M_PREC_MIXED ? pairs_impl<float>(c, acc_in, acc_out, kfac, kfac_dev)
+    return c->precision == P3M_PREC_MIXED ? pairs_x2_impl(c, acc_in, acc_out, kfac, kfac_dev)
                                           : pairs_impl<double>(c, acc_in, acc_out, kfac, kfac_dev);
 }

@@ -272,7 +272,7 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
                           const double *__restrict__ mom, const uint32_t *__restrict__ pid,
                           double *__restrict__ pos_out, double *__restrict__ mom_out,
                           uint32_t *__restrict__ pid_out, R4 *__restrict__ rel,
-                          float4 *__restrict__ block_box)
+                          float4 *__restrict__ block_box, float *__restrict__ relx)
 {
     // one warp per 32-slot block of the sorted order; the warp also writes the block's
     // bounding box (FP32, absolute coordinates, rounded outwards by the callers' margins)
@@ -286,6 +286,7 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
         const bool active = k < n;
         const uint32_t j = perm[active ? k : blk * 32];
         const double x = pos[j], y = pos[n + j], z = pos[2 * n + j];
+        R4 rv = make_rel<R4>(0.0, 0.0, 0.0);
         if (active) {
             pos_out[k] = x;
             pos_out[n + k] = y;
@@ -297,7 +298,14 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
             const uint32_t cell = keys[k] >> (3 * g.sub_bits);
             const uint32_t cx = cell % g.n_c, cy = (cell / g.n_c) % g.n_c,
                            cz = cell / (g.n_c * g.n_c);
-            rel[k] = rel_coords<R4>(x, y, z, cx, cy, cz, g.cs);
+            rv = rel_coords<R4>(x, y, z, cx, cy, cz, g.cs);
+            rel[k] = rv;
+        }
+        if (relx) {  // block-SoA copy of the relative coordinates (zero past the end)
+            float *dst = relx + blk * 96;
+            dst[lane] = (float)rv.x;
+            dst[32 + lane] = (float)rv.y;
+            dst[64 + lane] = (float)rv.z;
         }
         float lx = (float)x, ly = (float)y, lz = (float)z, hx = lx, hy = ly, hz = lz;
 #pragma unroll
@@ -462,11 +470,12 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     if (c->precision == P3M_PREC_MIXED)
         k_permute<float4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                      c->pid, c->pos_alt, c->mom_alt, c->pid_alt,
-                                                     (float4 *)c->rel, c->block_box);
+                                                     (float4 *)c->rel, c->block_box, c->relx);
     else
         k_permute<double4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                       c->pid, c->pos_alt, c->mom_alt,
-                                                      c->pid_alt, (double4 *)c->rel, c->block_box);
+                                                      c->pid_alt, (double4 *)c->rel, c->block_box,
+                                                      nullptr);
     double *t = c->pos;
     c->pos = c->pos_alt;
     c->pos_alt = t;
