@@ -282,6 +282,13 @@ def run_ours(args, rank, world, local_rank, dist):
                                                         if tk["bound"] == "alu" else "hbm_gbs"),
                     "traffic": _traffic(top)}
 
+    # measured FMA throughput of this GPU (library probe): cross-check of the derived ALU peak
+    from paper_1510_07621_gb300 import measure_fma_peak
+    fma32, fma64 = measure_fma_peak(False), measure_fma_peak(True)
+    if roofline is not None and roofline["bound"] == "alu":
+        roofline["measured_fma_peak"] = fma32
+        roofline["frac_of_measured_fma_peak"] = roofline["achieved"] / fma32
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -294,6 +301,7 @@ def run_ours(args, rank, world, local_rank, dist):
            "roofline": roofline, "kernels": kernels,
            "gpu_launches": int(d1["launches"] - d0["launches"]),
            "pairs_per_step": pairs_per_step, "max_cell_count": d1["max_cell_count"],
+           "fma_probe_tflops": {"fp32": fma32, "fp64": fma64},
            "clocks": clk}
 
     # ---- e2e through the C ABI with pinned host buffers (rank 0 measures, others idle)
@@ -332,6 +340,7 @@ def run_ours(args, rank, world, local_rank, dist):
             s64.step(a, a * (ratio - 1.0))
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0 = s64.diagnostics()["pairs_total"]
             e0.record(stream)
             a64 = a * ratio
             for _ in range(args.fp64_steps):
@@ -340,10 +349,14 @@ def run_ours(args, rank, world, local_rank, dist):
             e1.record(stream)
             torch.cuda.synchronize(dev)
             ms64 = e0.elapsed_time(e1) / args.fp64_steps
+            pairs64 = (s64.diagnostics()["pairs_total"] - p0) / args.fp64_steps
         rms = math.sqrt(float(np.sum((f32 - f64) ** 2) / np.sum(f64 ** 2)))
         out["fp64_gpu"] = {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                            "steps": args.fp64_steps,
                            "mixed_vs_fp64_force_rel_rms": rms,
+                           "pair_tflops": pairs64 * FLOPS_PER_PAIR / (ms64 / 1e3) / 1e12,
+                           "fp64_fma_peak_measured": fma64,
+                           "pair_frac_of_fp64_peak": pairs64 * FLOPS_PER_PAIR / (ms64 / 1e3) / 1e12 / fma64,
                            "speedup_mixed_over_fp64": value / world / (n / (ms64 / 1e3))}
         if snap_pos is None:
             snap_pos, snap_mom = hp.numpy().copy(), hm.numpy().copy()

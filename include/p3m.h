@@ -342,6 +342,16 @@ const char *p3m_phase_name(int i);
  * to start at zero): calls whose GPU work overlaps, on different streams or from different
  * host threads, race and corrupt each other's results.  Order them on one stream.
  */
+/*
+ * Measurement helper (no counterpart in the guide): the FMA throughput of the current GPU in
+ * TFLOP/s (an FMA counts 2 flops), FP32 (fp64 = 0) or FP64 (fp64 = 1), from independent
+ * multiply-add chains over 8 blocks of 256 threads per SM; best of two timed launches after
+ * a warm-up.  Allocates and frees a small device buffer and its own stream; synchronises.
+ * Used for the roofline of the pair kernels: FP32 bounds the mixed mode, FP64 the all-FP64
+ * mode.  Returns P3M_ECUDA on a CUDA error (*tflops = NaN).
+ */
+int p3m_measure_fma_peak(int fp64, double *tflops);
+
 #define P3M_NOALLOC_MAX_N 1048576
 int p3m_cell_sort_noalloc(const double *pos3n, int64_t n, double box, int n_c, int sub_bits,
                           uint32_t *keys_out, uint32_t *ids_out, uint32_t *cell_start_out,

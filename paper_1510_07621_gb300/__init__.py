@@ -51,6 +51,14 @@ def phase_names():
     return [lib.p3m_phase_name(i).decode() for i in range(_lib.P3M_NPHASES)]
 
 
+def measure_fma_peak(fp64: bool = False) -> float:
+    """Measured FMA throughput of the current GPU in TFLOP/s (FP32 or FP64)."""
+    lib = load()
+    t = ctypes.c_double()
+    check(lib.p3m_measure_fma_peak(1 if fp64 else 0, ctypes.byref(t)), None)
+    return t.value
+
+
 class P3M:
     """One P3M simulation context (box, N particles, mesh^3 PM grid).
 

@@ -85,6 +85,7 @@ SIGNATURES = {
     "p3m_autotune": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _vp]),
     "p3m_cell_sort_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_double, _c.c_int, _c.c_int,
                                          _vp, _vp, _vp, _vp]),
+    "p3m_measure_fma_peak": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_double)]),
     "p3m_last_error": (_c.c_char_p, [_vp]),
     "p3m_free": (None, [_vp]),
 }

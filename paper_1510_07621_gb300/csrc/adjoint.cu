@@ -224,9 +224,9 @@ __device__ __forceinline__ void pair_jac(float r2, float eps2, float inv_rs, con
     const float s = rsqrt_approx(r2 + eps2);
     const float r = r2 * t;
     const float tau = fmaf(r2, gp.c[11], -1.0f);
-    float p = gp.c[10];
+    float p = gp.c[P3M_SPLIT_DEG];
 #pragma unroll
-    for (int k = 9; k >= 0; --k) p = fmaf(p, tau, gp.c[k]);
+    for (int k = P3M_SPLIT_DEG - 1; k >= 0; --k) p = fmaf(p, tau, gp.c[k]);
     const float gval = fmaf(r2 * r, p, 1.0f);
     const float x = r * inv_rs;
     const float gder = -x * x * __expf(-0.25f * x * x) * 0.282094791773878143f;  // 1/(2 sqrt pi)
@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(32)
 {
     using V4 = typename V4Of<T>::type;
     constexpr bool kAbsolute = sizeof(T) == 8;
+    __shared__ NeighbourF nbr[27];  // FP32 mode: the item's neighbours, FP32 shifts
     const int lane = threadIdx.x;
     const int64_t n = g.n;
     const uint32_t n_work = *n_work_ptr;
@@ -288,37 +289,56 @@ __global__ void __launch_bounds__(32)
         const uint32_t cell = work[2 * (size_t)item], first = work[2 * (size_t)item + 1];
         const uint32_t cend = cell_start[cell + 1];
         const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
+        if (!kAbsolute) {
+            __syncwarp();  // the previous item is done with nbr
+            if (lane < 27) nbr[lane] = make_neighbour(g, cell_start, cx, cy, cz, lane);
+            __syncwarp();
+        }
         const uint32_t i = first + lane;
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
         const V4 xi = rel[ii];
         const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];
+        const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za;
         const T vix = (T)vs[ii], viy = (T)vs[n + ii], viz = (T)vs[2 * n + ii];
-        double o[3] = {0.0, 0.0, 0.0};
+        double o[3] = {0.0, 0.0, 0.0};             // FP64 mode
+        float so[3] = {0, 0, 0}, co[3] = {0, 0, 0};  // FP32 mode: TwoSum sum and compensation
         for (int nb = 0; nb < 27; ++nb) {
-            const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
-            const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
-            const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
-            const uint32_t js = cell_start[q], je = cell_start[q + 1];
-            if (js == je) continue;
-            const double L = g.box, cs = g.cs;
-            const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
-            const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
-            const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            uint32_t js, je;
             T xs, ys, zs, ix = 0, iy = 0, iz = 0;
+            float cxs, cys, czs;
             if (kAbsolute) {
+                const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
+                const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
+                const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
+                js = cell_start[q];
+                je = cell_start[q + 1];
+                if (js == je) continue;
+                const double L = g.box;
+                const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+                const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+                const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
                 xs = (T)xi.x;
                 ys = (T)xi.y;
                 zs = (T)xi.z;
                 ix = (T)imx;
                 iy = (T)imy;
                 iz = (T)imz;
+                cxs = (float)(xa - imx);
+                cys = (float)(ya - imy);
+                czs = (float)(za - imz);
             } else {
-                xs = (T)((double)xi.x - (((double)wx * cs + imx) - (double)cx * cs));
-                ys = (T)((double)xi.y - (((double)wy * cs + imy) - (double)cy * cs));
-                zs = (T)((double)xi.z - (((double)wz * cs + imz) - (double)cz * cs));
+                const NeighbourF &q = nbr[nb];
+                js = q.start;
+                je = q.end;
+                if (js == je) continue;
+                xs = (T)(((float)xi.x - q.sx) - q.rx);
+                ys = (T)(((float)xi.y - q.sy) - q.ry);
+                zs = (T)(((float)xi.z - q.sz) - q.rz);
+                cxs = xaf - q.imx;
+                cys = yaf - q.imy;
+                czs = zaf - q.imz;
             }
-            const float cxs = (float)(xa - imx), cys = (float)(ya - imy), czs = (float)(za - imz);
             T ox = 0, oy = 0, oz = 0;
             for (uint32_t b = js >> 5; b * 32u < je; ++b) {
                 const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
@@ -372,10 +392,18 @@ __global__ void __launch_bounds__(32)
                     oz += hh * w2 + c * dz;
                 }
             }
-            o[0] += (double)ox;
-            o[1] += (double)oy;
-            o[2] += (double)oz;
+            if (kAbsolute) {
+                o[0] += (double)ox;
+                o[1] += (double)oy;
+                o[2] += (double)oz;
+            } else {
+                two_sum_add(so[0], co[0], (float)ox);
+                two_sum_add(so[1], co[1], (float)oy);
+                two_sum_add(so[2], co[2], (float)oz);
+            }
         }
+        if (!kAbsolute)
+            for (int d = 0; d < 3; ++d) o[d] = (double)so[d] + (double)co[d];
         if (valid) {
             out[i] += g.gm * o[0];
             out[n + i] += g.gm * o[1];

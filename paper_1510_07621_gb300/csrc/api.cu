@@ -91,7 +91,7 @@ double quad(const p3m_cosmology &cs, double a1, double a2, int power)
 // ---------------------------------------------------------------- split factor fit
 // g(x) = erfc(x/2) + x/sqrt(pi) exp(-x^2/4) = 1 + x^3 Q(x^2).  Q is smooth in u = x^2; it is
 // interpolated at 40 Chebyshev-Gauss nodes of u in [0, u_c], u_c = (r_c/r_s)^2, truncated to
-// degree 10 (a near-minimax polynomial), and rewritten in monomial form in tau = 2u/u_c - 1
+// degree P3M_SPLIT_DEG (a near-minimax polynomial), and rewritten in monomial form in tau = 2u/u_c - 1
 // for Horner evaluation in FP32.  The kernel evaluates g = 1 + r^3 Q'(tau) directly from
 // r^2, so the coefficients are scaled by r_s^-3 and tau = r^2 (2 / (u_c r_s^2)) - 1.
 
@@ -105,7 +105,7 @@ double split_q(double u)
 
 void fit_split_poly(double cutoff_in_rs, double r_s, float out[12])
 {
-    const int deg = 10, nodes = 40;
+    const int deg = P3M_SPLIT_DEG, nodes = 40;
     const double uc = cutoff_in_rs * cutoff_in_rs;
     double cheb[deg + 1] = {0};
     for (int j = 0; j < nodes; ++j) {
@@ -133,6 +133,7 @@ void fit_split_poly(double cutoff_in_rs, double r_s, float out[12])
     }
     const double inv_rs3 = 1.0 / (r_s * r_s * r_s);
     for (int i = 0; i <= deg; ++i) out[i] = (float)(mono[i] * inv_rs3);
+    for (int i = deg + 1; i < 11; ++i) out[i] = 0.0f;
     out[11] = (float)(2.0 / (uc * r_s * r_s));
 }
 

@@ -206,3 +206,72 @@ cudaError_t launch_diag(p3m_ctx *c, double *host_out)
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(c->stream);
 }
+
+// ------------------------------------------------------------------ FMA throughput probe
+// Independent multiply-add chains (8 per thread) over many resident warps: the measured
+// FP32 / FP64 FMA rate of this GPU, for the roofline of the pair kernels.
+
+namespace {
+
+constexpr int kProbeChains = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T *out, T seed, int iters)
+{
+    T a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = seed + (T)k;
+    const T b = (T)0.9999999, c = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], b, c);
+    }
+    T t = 0;
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) t += a[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = t;  // keeps the chains alive
+}
+
+template <typename T>
+int fma_probe(int iters, double *tflops)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return P3M_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return P3M_ECUDA;
+    const int threads = 256, blocks = sms * 8;
+    const size_t nt = (size_t)threads * blocks;
+    T *out = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, nt * sizeof(T));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {  // first launch warms up
+        e = cudaEventRecord(e0, s);
+        k_fma_probe<T><<<blocks, threads, 0, s>>>(out, (T)1, iters);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    if (e == cudaSuccess && best > 0.0f)
+        *tflops = 2.0 * kProbeChains * (double)iters * (double)nt / (best * 1e-3) / 1e12;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (out) cudaFree(out);
+    return e == cudaSuccess ? P3M_OK : P3M_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int p3m_measure_fma_peak(int fp64, double *tflops)
+{
+    if (!tflops) return P3M_EINVAL;
+    *tflops = NAN;
+    return fp64 ? fma_probe<double>(256, tflops) : fma_probe<float>(8192, tflops);
+}

@@ -69,8 +69,8 @@ struct p3m_ctx {
     double *tab_one;               // M ones (no deconvolution)
     double *ps_acc;                // power spectrum partial sums (3 * (M/2) + 1)
     double green_const;
-    float gpoly[12];  // FP32 split factor: g = 1 + x u Q(tau), Q = sum gpoly[k] tau^k (k <= 10),
-                      // tau = u gpoly[11] - 1, u = (r/r_s)^2
+    float gpoly[12];  // FP32 split factor: g = 1 + r^3 Q(tau), Q = sum gpoly[k] tau^k
+                      // (k <= P3M_SPLIT_DEG), tau = r^2 gpoly[11] - 1
     cufftHandle plan_r2c, plan_c2r, plan_c2r_one;  // R2C, batched 3 x C2R, single C2R
     bool plans_made;
 
@@ -126,9 +126,69 @@ enum {
 
 #define P3M_MAX_GRAPH_STEPS 4096  // steps per p3m_run_steps / p3m_ensemble_run call
 #define P3M_SORT_TILE 4096   // keys per radix-sort tile (256 threads x 16)
+// Degree of the fitted FP32 split factor Q (Chebyshev fit on [0, r_c]).  Its largest error in g
+// is 5.8e-6 (near r_c, where g = 0.0175).  Against the FP64 oracle the FP32 short-range force
+// then differs by 7.50e-6 relative RMS on the 32^3 Zel'dovich state at a = 0.02 (7.31e-6 at
+// degree 10, 1.8e-5 at degree 7: the FP32 rounding of nearly cancelling pair sums dominates)
+// and by 1.7e-6 on a clustered state.
+#define P3M_SPLIT_DEG 8
 #define P3M_PAIR_TI 32       // i-particles per pair work item (one per lane of a warp)
 #define P3M_PAIR_TJ 128      // j-particles per shared-memory tile (4 blocks of 32)
 #define P3M_FLAG_TIMEOUT 1u  // counters[1] bit: a bounded wait gave up
+
+// A neighbour cell of a pair work item, for the FP32 pair kernels: the shift between the two
+// cells' origins (periodic image included) as an FP32 value plus the FP32 residual of the FP64
+// shift, the periodic image alone, and the neighbour's range of sorted slots.
+struct NeighbourF {
+    uint32_t start, end;
+    float sx, sy, sz, rx, ry, rz;
+    float imx, imy, imz, pad;
+};
+
+// Neighbour nb (0..26, offsets (nb%3-1, nb/3%3-1, nb/9-1)) of cell (cx, cy, cz); an empty
+// neighbour gets start = end = 0.
+__device__ __forceinline__ NeighbourF make_neighbour(const P3MGeom &g, const uint32_t *cell_start,
+                                                     int cx, int cy, int cz, int nb)
+{
+    const int nc = g.n_c;
+    const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
+    const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
+    const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
+    NeighbourF r;
+    r.start = cell_start[q];
+    r.end = cell_start[q + 1];
+    if (r.start == r.end) r.start = r.end = 0;
+    const double L = g.box, cs = g.cs;
+    const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+    const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+    const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+    const double sx = ((double)wx * cs + imx) - (double)cx * cs;
+    const double sy = ((double)wy * cs + imy) - (double)cy * cs;
+    const double sz = ((double)wz * cs + imz) - (double)cz * cs;
+    r.sx = (float)sx;
+    r.sy = (float)sy;
+    r.sz = (float)sz;
+    r.rx = (float)(sx - (double)r.sx);
+    r.ry = (float)(sy - (double)r.sy);
+    r.rz = (float)(sz - (double)r.sz);
+    r.imx = (float)imx;
+    r.imy = (float)imy;
+    r.imz = (float)imz;
+    r.pad = 0.0f;
+    return r;
+}
+
+// s + c += x, Knuth's TwoSum: the FP32 sum s and the running compensation c keep the rounding
+// error of every addition, so partial sums add up as accurately as in FP64 without using
+// GB300's narrow FP64 pipe.
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += e;
+}
 #define P3M_FLAG_NONFINITE 2u
 
 // ------------------------------------------------------------------ launchers (sort.cu)

@@ -100,6 +100,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float y;
@@ -108,7 +115,7 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 }
 
 // Coefficients of the FP32 split factor, fitted on the host for the context's cutoff:
-// g = 1 + r^3 sum_k c[k] tau^k (k = 0..10), tau = r^2 c[11] - 1.
+// g = 1 + r^3 sum_k c[k] tau^k (k = 0..P3M_SPLIT_DEG), tau = r^2 c[11] - 1.
 struct GPoly {
     float c[12];
 };
@@ -387,26 +394,6 @@ __global__ void __launch_bounds__(32)
 
 typedef unsigned long long f2;
 
-// A neighbour cell for the FP32 kernel: its shift as an FP32 value plus the FP32 residual of
-// the FP64 shift (the pair (sx, rx) carries the FP64 value to ~2^-48), and its periodic image.
-struct NeighbourF {
-    uint32_t start, end;
-    float sx, sy, sz, rx, ry, rz;
-    float imx, imy, imz, pad;
-};
-
-// s + c += x, Knuth's TwoSum: the FP32 sum s and the running compensation c keep the rounding
-// error of every addition, so the per-tile partial sums add up as accurately as in FP64
-// without touching the (slow) FP64 pipe inside the tile loop.
-__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
-{
-    const float t = s + x;
-    const float bp = t - s;
-    const float e = (s - (t - bp)) + (x - bp);
-    s = t;
-    c += e;
-}
-
 __device__ __forceinline__ f2 f2_pack(float lo, float hi)
 {
     f2 r;
@@ -446,7 +433,7 @@ constexpr float kTiny = 1e-20f;
 
 // Per-lane constants of the packed evaluation.
 struct PairConst2 {
-    f2 c[11];    // polynomial coefficients, both halves equal
+    f2 c[P3M_SPLIT_DEG + 1];  // polynomial coefficients, both halves equal
     f2 c11, m1, one, eps2, tiny;
 };
 
@@ -457,13 +444,12 @@ __device__ __forceinline__ f2 pair_factor2(f2 r2, const PairConst2 &k)
     const f2 s2 = f2_add(r2, k.eps2);
     f2_unpack(r2, r2l, r2h);
     f2_unpack(s2, s2l, s2h);
-    const f2 t = f2_pack(rsqrt_approx(r2l), rsqrt_approx(r2h));
     const f2 s = f2_pack(rsqrt_approx(s2l), rsqrt_approx(s2h));
-    const f2 r3 = f2_mul(r2, f2_mul(r2, t));
+    const f2 r3 = f2_mul(r2, f2_pack(sqrt_approx(r2l), sqrt_approx(r2h)));
     const f2 tau = f2_fma(r2, k.c11, k.m1);
-    f2 p = k.c[10];
+    f2 p = k.c[P3M_SPLIT_DEG];
 #pragma unroll
-    for (int q = 9; q >= 0; --q) p = f2_fma(p, tau, k.c[q]);
+    for (int q = P3M_SPLIT_DEG - 1; q >= 0; --q) p = f2_fma(p, tau, k.c[q]);
     const f2 gval = f2_fma(r3, p, k.one);
     return f2_mul(gval, f2_mul(f2_mul(s, s), s));
 }
@@ -492,7 +478,7 @@ __global__ void __launch_bounds__(32)
     const int nc = g.n_c;
     PairConst2 kc;
 #pragma unroll
-    for (int q = 0; q < 11; ++q) kc.c[q] = f2_pack(gp.c[q], gp.c[q]);
+    for (int q = 0; q <= P3M_SPLIT_DEG; ++q) kc.c[q] = f2_pack(gp.c[q], gp.c[q]);
     kc.c11 = f2_pack(gp.c[11], gp.c[11]);
     kc.m1 = f2_pack(-1.0f, -1.0f);
     kc.one = f2_pack(1.0f, 1.0f);
@@ -521,34 +507,7 @@ __global__ void __launch_bounds__(32)
         const uint32_t first = work[2 * (size_t)item + 1];
         const uint32_t cend = cell_start[cell + 1];
         const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
-        if (lane < 27) {
-            const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
-            const int ux = cx + ox, uy = cy + oy, uz = cz + oz;
-            const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
-            const uint32_t nb = ((uint32_t)wz * nc + wy) * nc + wx;
-            NeighbourF q;
-            q.start = cell_start[nb];
-            q.end = cell_start[nb + 1];
-            if (q.start == q.end) q.start = q.end = 0;  // empty: the tile walk skips it
-            const double L = g.box, cs = g.cs;
-            const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
-            const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
-            const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
-            const double sx = ((double)wx * cs + imx) - (double)cx * cs;
-            const double sy = ((double)wy * cs + imy) - (double)cy * cs;
-            const double sz = ((double)wz * cs + imz) - (double)cz * cs;
-            q.sx = (float)sx;
-            q.sy = (float)sy;
-            q.sz = (float)sz;
-            q.rx = (float)(sx - (double)q.sx);
-            q.ry = (float)(sy - (double)q.sy);
-            q.rz = (float)(sz - (double)q.sz);
-            q.imx = (float)imx;
-            q.imy = (float)imy;
-            q.imz = (float)imz;
-            q.pad = 0.0f;
-            nbr[lane] = q;
-        }
+        if (lane < 27) nbr[lane] = make_neighbour(g, cell_start, cx, cy, cz, lane);
         __syncwarp();
 
         const uint32_t i = first + lane;
@@ -623,6 +582,38 @@ __global__ void __launch_bounds__(32)
                 cnt += (inl && r2l > kTiny) + (inh && r2h > kTiny);
             };
 
+            // two aligned pairs (p, p+1) and (p+2, p+3), all four halves taking part: each
+            // pair is skipped when no lane accepts it, and when both are needed their
+            // evaluations interleave
+            auto pairs_tested2 = [&](const float *bx, uint32_t p) {
+                f2 d[2][3], r2[2];
+                bool in[2][2], any[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    d[u][0] = f2_sub(*(const f2 *)(bx + p + 2 * u), xs2);
+                    d[u][1] = f2_sub(*(const f2 *)(bx + 32 + p + 2 * u), ys2);
+                    d[u][2] = f2_sub(*(const f2 *)(bx + 64 + p + 2 * u), zs2);
+                    r2[u] = f2_fma(d[u][2], d[u][2], f2_fma(d[u][1], d[u][1], f2_fma(d[u][0], d[u][0], kc.tiny)));
+                    float l, h;
+                    f2_unpack(r2[u], l, h);
+                    in[u][0] = l < rc2;
+                    in[u][1] = h < rc2;
+                    any[u] = __any_sync(0xffffffffu, in[u][0] || in[u][1]);
+                    cnt += (in[u][0] && l > kTiny) + (in[u][1] && h > kTiny);
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (!any[u]) continue;
+                    ++n_eval;
+                    float fl, fh;
+                    f2_unpack(pair_factor2(r2[u], kc), fl, fh);
+                    const f2 f = f2_pack(in[u][0] ? fl : 0.0f, in[u][1] ? fh : 0.0f);
+                    px = f2_fma(f, d[u][0], px);
+                    py = f2_fma(f, d[u][1], py);
+                    pz = f2_fma(f, d[u][2], pz);
+                }
+            };
+
             for (uint32_t b = b_c; b < bend; ++b) {
                 const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
                 const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
@@ -669,6 +660,7 @@ __global__ void __launch_bounds__(32)
                     pair_tested(bx, p, false, true);
                     p += 2;
                 }
+                for (; p + 3 < j1; p += 4) pairs_tested2(bx, p);
                 for (; p + 1 < j1; p += 2) pair_tested(bx, p, true, true);
                 if (p < j1) pair_tested(bx, p, true, false);
             }
