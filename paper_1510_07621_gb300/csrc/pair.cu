@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kTJ = P3M_PAIR_TJ;  // 128
 constexpr int kBlocksPerTile = kTJ / 32;
+constexpr int kBlocksPerTileX2 = 4;  // FP32 kernel: 128 j particles (1.5 KB) per tile
 
 template <typename T>
 struct Vec4;
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(32)
 {
     constexpr int kBlockFloats = 96;  // x[32] y[32] z[32]
     if (kfac_dev) kfac = *kfac_dev;
-    __shared__ __align__(128) float sj[2][kBlocksPerTile * kBlockFloats];
+    __shared__ __align__(128) float sj[2][kBlocksPerTileX2 * kBlockFloats];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ NeighbourF nbr[27];
 
@@ -526,7 +527,7 @@ __global__ void __launch_bounds__(32)
             }
         };
         auto issue = [&](int nb, uint32_t b, int to) {
-            const uint32_t bend = min(b + kBlocksPerTile, (nbr[nb].end + 31) >> 5);
+            const uint32_t bend = min(b + kBlocksPerTileX2, (nbr[nb].end + 31) >> 5);
             const uint32_t bytes = (bend - b) * (uint32_t)(kBlockFloats * sizeof(float));
             mbar_expect_tx(&bar[to], bytes);
             bulk_load(&sj[to][0], relx + (size_t)b * kBlockFloats, bytes, &bar[to]);
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(32)
         if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
         while (nb_c < 27) {
             const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
-            const uint32_t bend = min(b_c + kBlocksPerTile, (nend + 31) >> 5);
+            const uint32_t bend = min(b_c + kBlocksPerTileX2, (nend + 31) >> 5);
             int nb_n = nb_c;
             uint32_t b_n = bend;
             next_tile(nb_n, b_n);
