@@ -909,6 +909,8 @@ struct p3m_ensemble {
     cudaStream_t *own;        // streams the ensemble created for its contexts (or NULL)
     cudaEvent_t fork, *join;  // fork/join of the captured branches
     cudaGraphExec_t gexec[2]; // one captured step for each step parity
+    cudaGraphExec_t gchunk;   // kChunkSteps steps from parity 0: the contexts do not meet
+                              // between these steps, so a short simulation runs ahead
     bool ready;
     int parity;               // parity of the next step to replay
     PtrState *state[2];       // per context: buffer roles before an even / odd step
@@ -917,8 +919,11 @@ struct p3m_ensemble {
 
 namespace {
 
-// Captures one step of every context as parallel branches of one graph.
-int capture_step(p3m_ensemble *e, int parity)
+constexpr int kChunkSteps = 8;  // steps per chunk graph (even: buffer roles have period 2)
+
+// Captures `steps` consecutive steps of every context as parallel branches of one graph
+// (one branch per context, its steps in sequence) into *out.
+int capture_steps(p3m_ensemble *e, int steps, cudaGraphExec_t *out)
 {
     p3m_ctx *c = nullptr;
     cudaGraph_t graph = nullptr;
@@ -932,7 +937,7 @@ int capture_step(p3m_ensemble *e, int parity)
         err = cudaStreamWaitEvent(c->stream, e->fork, 0);
         if (err != cudaSuccess) break;
         c->capturing = true;
-        rc = step_body(c, 0.0, 0.0, true);
+        for (int k = 0; k < steps && rc == P3M_OK; ++k) rc = step_body(c, 0.0, 0.0, true);
         c->capturing = false;
         if (rc == P3M_OK) err = cudaEventRecord(e->join[i], c->stream);
         if (err == cudaSuccess && rc == P3M_OK) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
@@ -943,7 +948,7 @@ int capture_step(p3m_ensemble *e, int parity)
         return p3m_fail_global(rc, "graph capture: %s", c ? c->err : "step failed");
     }
     if (err == cudaSuccess) err = end;
-    if (err == cudaSuccess) err = cudaGraphInstantiate(&e->gexec[parity], graph, 0);
+    if (err == cudaSuccess) err = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (err != cudaSuccess)
         return p3m_fail_global(P3M_ECUDA, "graph capture: %s", cudaGetErrorString(err));
@@ -957,6 +962,10 @@ void drop_graphs(p3m_ensemble *e)
             cudaGraphExecDestroy(e->gexec[p]);
             e->gexec[p] = nullptr;
         }
+    if (e->gchunk) {
+        cudaGraphExecDestroy(e->gchunk);
+        e->gchunk = nullptr;
+    }
     e->ready = false;
 }
 
@@ -1063,9 +1072,13 @@ extern "C" int p3m_ensemble_run(p3m_ensemble *e, const double *a_list, int n_ste
                 e->state[0][i] = save_ptrs(e->c[i]);
                 e->version[i] = e->c[i]->geom_version;
             }
-            int rc = capture_step(e, 0);
+            int rc = capture_steps(e, 1, &e->gexec[0]);
             for (int i = 0; i < e->n && rc == P3M_OK; ++i) e->state[1][i] = save_ptrs(e->c[i]);
-            if (rc == P3M_OK) rc = capture_step(e, 1);
+            if (rc == P3M_OK) rc = capture_steps(e, 1, &e->gexec[1]);
+            // back at the parity-0 roles: the chunk graph starts there and ends there
+            for (int i = 0; i < e->n && rc == P3M_OK; ++i)
+                if (!(save_ptrs(e->c[i]) == e->state[0][i])) rc = P3M_ESTATE;
+            if (rc == P3M_OK) rc = capture_steps(e, kChunkSteps, &e->gchunk);
             if (rc != P3M_OK) {
                 for (int i = 0; i < e->n; ++i) load_ptrs(e->c[i], e->state[0][i]);
                 drop_graphs(e);
@@ -1075,9 +1088,15 @@ extern "C" int p3m_ensemble_run(p3m_ensemble *e, const double *a_list, int n_ste
             e->parity = 0;
         }
         cudaError_t err = cudaSuccess;
-        for (int k = 0; k < n_steps && err == cudaSuccess; ++k) {
-            err = cudaGraphLaunch(e->gexec[e->parity], e->parent);
-            e->parity ^= 1;
+        for (int k = 0; k < n_steps && err == cudaSuccess;) {
+            if (e->parity == 0 && n_steps - k >= kChunkSteps) {
+                err = cudaGraphLaunch(e->gchunk, e->parent);
+                k += kChunkSteps;
+            } else {
+                err = cudaGraphLaunch(e->gexec[e->parity], e->parent);
+                e->parity ^= 1;
+                ++k;
+            }
         }
         // later work on the contexts' own streams comes after the replayed steps
         if (err == cudaSuccess) err = cudaEventRecord(e->fork, e->parent);

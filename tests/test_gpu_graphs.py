@@ -35,11 +35,11 @@ def test_graph_steps_follow_host_steps(mod, precision):
     their FP32 rounding, which close pairs amplify; rms within 1e-7 L, worst within 1e-5 L."""
     torch, m = mod
     pos, mom = S.zeldovich(32, 64.0, 0.02, 1511)
-    a = S.log_spaced_steps(0.02, 0.1, 10)
+    a = S.log_spaced_steps(0.02, 0.1, 14)
     n = pos.shape[1]
     ref = m.P3M(64.0, n, 32, stream=0, precision=precision)
     ref.set_particles(pos, mom, a=a[0])
-    for k in range(10):
+    for k in range(14):
         ref.step(a[k], a[k + 1] - a[k])
     rp, rm = ref.get_particles()
     s = torch.cuda.Stream()
@@ -47,7 +47,7 @@ def test_graph_steps_follow_host_steps(mod, precision):
         sim.set_particles(pos, mom, a=a[0])
         sim.run_steps(a[:4], use_graph=True)     # 3 steps: odd, parity flips
         sim.step(a[3], a[4] - a[3])              # host step in between: graphs recaptured
-        sim.run_steps(a[4:], use_graph=True)     # 6 more
+        sim.run_steps(a[4:], use_graph=True)     # 10 more: an 8-step chunk graph + 2 single
         gp, gm = sim.get_particles()
         d = sim.diagnostics()
     ref.close()
@@ -65,13 +65,13 @@ def test_graph_steps_follow_host_steps(mod, precision):
 def test_ensemble_matches_individual_runs(mod):
     torch, m = mod
     specs = [(16, 32.0, 32, 11), (24, 40.0, 24, 12), (32, 64.0, 32, 13)]
-    a = S.log_spaced_steps(0.05, 0.2, 5)
+    a = S.log_spaced_steps(0.05, 0.2, 12)
     ics = [S.zeldovich(n_p, box, a[0], seed) for n_p, box, mesh, seed in specs]
     refs = []
     for (n_p, box, mesh, seed), (pos, mom) in zip(specs, ics):
         with m.P3M(box, n_p ** 3, mesh, stream=0, precision="fp64") as r:
             r.set_particles(pos, mom, a=a[0])
-            for k in range(5):
+            for k in range(12):
                 r.step(a[k], a[k + 1] - a[k])
             refs.append(r.get_particles())
     for use_graph in (True, False):
@@ -80,8 +80,8 @@ def test_ensemble_matches_individual_runs(mod):
         for s_, (pos, mom) in zip(sims, ics):
             s_.set_particles(pos, mom, a=a[0])
         with m.Ensemble(sims) as ens:
-            ens.run(a[:3], use_graph=use_graph)
-            ens.run(a[2:], use_graph=use_graph)
+            ens.run(a[:3], use_graph=use_graph)   # 2 single-step graphs
+            ens.run(a[2:], use_graph=use_graph)   # one 8-step chunk graph, then 2 single steps
         for s_, (n_p, box, mesh, seed), (rp, rm) in zip(sims, specs, refs):
             gp, gm = s_.get_particles()
             assert _max_dx(gp, rp, box) < 1e-11 * box
