@@ -552,6 +552,66 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- 512^3 Zel'dovich
+
+
+Z512_NAME = ("zeldovich512: 512^3 particles, 512^3 mesh, box 1000 Mpc/h, r_s 1.25 cells, cutoff "
+             "4.5 r_s, softening 0.02, EdS; seeded Zel'dovich ICs at a=0.5 (seed 1513), one force "
+             "evaluation, then 10 log-spaced steps a=0.5->1")
+
+
+def run_zeldovich512(args):
+    """The largest configuration: 134 M particles, one force evaluation and 10 steps timed
+    with CUDA events on the library's stream."""
+    import torch
+    from paper_1510_07621_gb300 import P3M, build
+
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n_p, box = 512, 1000.0
+    n = n_p ** 3
+    pos, mom = S.zeldovich(n_p, box, 0.5, 1513)
+    a = S.log_spaced_steps(0.5, 1.0, 10)
+    out = {}
+    with P3M(box, n, n_p, softening=0.02, stream=stream) as sim:
+        dpos = torch.from_numpy(pos).cuda()
+        dmom = torch.from_numpy(mom).cuda()
+        del pos, mom
+        sim.set_particles(dpos, dmom, a=a[0])
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        sim.set_timing(True)
+        sim.timings(reset=True)
+        d0 = sim.diagnostics()
+        e0.record(stream)
+        sim.forces(a[0])
+        e1.record(stream)
+        for k in range(10):
+            sim.step(a[k], a[k + 1] - a[k])
+        e2.record(stream)
+        torch.cuda.synchronize()
+        phases = sim.timings(reset=True)
+        d1 = sim.diagnostics()
+    ms_force = e0.elapsed_time(e1)
+    ms_steps = e1.elapsed_time(e2)
+    pairs = d1["pairs_total"] - d0["pairs_total"]
+    alu_peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * \
+        _peaks()[0].get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = pairs * FLOPS_PER_PAIR / (phases["pairs"] / 1e3) / 1e12
+    value = n * 10 / (ms_steps / 1e3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 10,
+            "warmup": 0, "ms_per_step": ms_steps / 10, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 forces, f64 positions/momenta",
+            "data": "synthetic", "config": {"workload": Z512_NAME, "particles": n, "mesh": n_p},
+            "force_evaluation_ms": ms_force, "phase_ms_total": phases,
+            "roofline": {"kernel": "pairs", "bound": "alu", "achieved": achieved,
+                         "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                         "traffic": None},
+            "pairs_per_step": pairs / 11, "max_cell_count": d1["max_cell_count"],
+            "gpu_launches": int(d1["launches"] - d0["launches"])}
+
+
 # ---------------------------------------------------------------- main
 
 
@@ -562,7 +622,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--workload", choices=["clustered_128", "ensemble48", "adjoint128"],
+    ap.add_argument("--workload", choices=["clustered_128", "ensemble48", "adjoint128",
+                                           "zeldovich512"],
                     default="clustered_128")
     ap.add_argument("--sub-bits", type=int, default=None,
                     help="Morton bits per axis inside a chaining cell (library default if unset)")
@@ -583,9 +644,10 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.workload in ("ensemble48", "adjoint128"):
+    if args.workload in ("ensemble48", "adjoint128", "zeldovich512"):
         if rank == 0:
-            fn = run_ensemble if args.workload == "ensemble48" else run_adjoint
+            fn = {"ensemble48": run_ensemble, "adjoint128": run_adjoint,
+                  "zeldovich512": run_zeldovich512}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
 
