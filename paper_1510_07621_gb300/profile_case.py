@@ -5,6 +5,7 @@
 Workloads (seeded, synthetic):
   evolved_128    128^3 Zel'dovich ICs (box 200, mesh 128) evolved 64 log steps a=0.02->1
   clustered_128  the synthetic clustered 128^3 stand-in snapshot (no evolution)
+  uniform_128    128^3 Zel'dovich ICs at a = 0.02 (box 200, mesh 128): near-uniform cells
   eds_32         32^3 Zel'dovich ICs at a = 0.02 (box 64, mesh 32)
   zeldovich_512  512^3 Zel'dovich ICs at a = 0.5 (box 1000, mesh 512)
 Prints the per-phase times (CUDA events) of the evaluations.
@@ -28,16 +29,20 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="evolved_128",
-                    choices=["evolved_128", "clustered_128", "eds_32", "zeldovich_512"])
+                    choices=["evolved_128", "clustered_128", "uniform_128", "eds_32",
+                             "zeldovich_512"])
     ap.add_argument("--evals", type=int, default=2)
     ap.add_argument("--steps", action="store_true", help="time steps instead of force evaluations")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     build.build()
-    if args.workload in ("evolved_128", "clustered_128"):
+    if args.workload in ("evolved_128", "clustered_128", "uniform_128"):
         box, n_p, mesh, a = 200.0, 128, 128, 1.0
         if args.workload == "evolved_128":
             pos, mom = S.zeldovich(n_p, box, 0.02, 1512)
+        elif args.workload == "uniform_128":
+            a = 0.02
+            pos, mom = S.zeldovich(n_p, box, a, 1512)
         else:
             pos, mom = S.clustered(n_p, box, 1512)
     elif args.workload == "eds_32":
@@ -66,7 +71,10 @@ def main():
     t = sim.timings(reset=True)
     d = sim.diagnostics()
     print(json.dumps({"workload": args.workload, "evals": args.evals, "phase_ms": t,
-                      "pairs": d["pairs"], "max_cell_count": d["max_cell_count"]}))
+                      "pairs": d["pairs"], "max_cell_count": d["max_cell_count"],
+                      "pair_warp_j_total": d["pair_warp_j"],
+                      "pair_blocks_culled_total": d["pair_blocks_culled"],
+                      "pair_tiles_total": d["pair_tiles"]}))
     sim.close()
 
 
