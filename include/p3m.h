@@ -215,6 +215,18 @@ typedef struct p3m_ensemble p3m_ensemble;
 int p3m_ensemble_create(p3m_ensemble **ens, p3m_ctx *const *ctxs, int n_ctx, int own_streams);
 int p3m_ensemble_run(p3m_ensemble *ens, const double *a_list, int n_steps, int use_graph);
 void p3m_ensemble_free(p3m_ensemble *ens);
+/*
+ * Batched pair launch (off by default; enable != 0 turns it on when at least one context is an
+ * FP32 P3M context): each step runs the contexts' phases up to the mesh force as parallel
+ * branches, then merges their pair work lists into one list sorted by estimated cost and
+ * evaluates every such context's pair sum in one persistent kernel launch (the contexts'
+ * arguments read from a device table).  Other contexts step as before.  Results equal the
+ * per-context launches up to the FP32 rounding of the mesh deposit's atomics.  Every step then
+ * waits for all contexts' mesh phases before the pair launch, which on the 48-simulation
+ * ensemble of 48^3..96^3 particles cost more than the shared launch saved (277 M against 285 M
+ * particle-updates/s with graphs); enable = 0 returns to independent per-context branches.
+ */
+int p3m_ensemble_set_batched(p3m_ensemble *ens, int enable);
 
 /*
  * Autotuner of the sort key's Morton depth: times two force evaluations of the current

@@ -321,6 +321,35 @@ int step_body(p3m_ctx *c, double a, double da, bool from_table)
     return P3M_OK;
 }
 
+// The part of a step that precedes the pair sum, for a context whose pair sum runs in the
+// ensemble's batched launch: kick-drift, sort, mesh force, then its pair arguments into
+// *desc and its cost-sorted work list into the merged arrays gk/gv (slot `slot`).
+int step_pre(p3m_ctx *c, double a, double da, bool from_table, int slot, PairArgs *desc,
+             uint32_t *gk, uint32_t *gv)
+{
+    double k1 = 0.0, dfac = 0.0, k2 = 0.0;
+    if (from_table) {
+        CK(launch_step_begin(c));
+    } else {
+        const double am = a + 0.5 * da, a2 = a + da;
+        k1 = c->mass * p3m_kick_factor(c->cosmo, a, am);
+        dfac = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
+        k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+    }
+    {
+        Phase ph(c, PH_KICK_DRIFT);
+        CK(launch_kick_drift_keys(c, true, k1, dfac, from_table));
+    }
+    int rc = evaluate(c, k2, nullptr, from_table, false);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream));
+    c->launches += 2;
+    CK(launch_store_pair_args(desc, pair_args(c, c->acc_lr, c->acc, k2, from_table ? c->cur_fac + 2 : nullptr),
+                              c->stream));
+    CK(launch_ens_gather(slot, c->work_key, c->work_order, c->max_work, gk, gv, c->stream));
+    return P3M_OK;
+}
+
 // Buffers whose roles swap during a step (all return to their roles after two steps).
 struct PtrState {
     double *pos, *mom, *pos_alt, *mom_alt;
@@ -915,6 +944,19 @@ struct p3m_ensemble {
     int parity;               // parity of the next step to replay
     PtrState *state[2];       // per context: buffer roles before an even / odd step
     int *version;             // per context: geometry version the graphs were captured with
+
+    // Batched pair launch: the FP32 P3M contexts' work items merged into one cost-sorted list
+    // and evaluated by one persistent pair kernel per step.
+    bool batched;             // on (default when at least two contexts qualify)
+    int nb;                   // contexts that qualify (FP32, short range)
+    int *slot;                // per context: its index among them, or -1
+    size_t *base;             // per qualifying context: offset of its work list in gkey/gval
+    size_t cap;               // sum of the qualifying contexts' work-list capacities
+    PairArgs *descs;          // device: pair arguments per qualifying context
+    const uint32_t **nwork;   // device: per qualifying context, its work-item count pointer
+    uint32_t *gkey[2], *gval[2], *gcounts, *gaux, *gtotal, *gcursor;
+    cudaEvent_t after_pairs;
+    unsigned long long launches;
 };
 
 namespace {
@@ -923,6 +965,8 @@ constexpr int kChunkSteps = 8;  // steps per chunk graph (even: buffer roles hav
 
 // Captures `steps` consecutive steps of every context as parallel branches of one graph
 // (one branch per context, its steps in sequence) into *out.
+int ens_step(p3m_ensemble *e, double a, double da, bool from_table);
+
 int capture_steps(p3m_ensemble *e, int steps, cudaGraphExec_t *out)
 {
     p3m_ctx *c = nullptr;
@@ -930,28 +974,89 @@ int capture_steps(p3m_ensemble *e, int steps, cudaGraphExec_t *out)
     cudaError_t err = cudaStreamBeginCapture(e->parent, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess)
         return p3m_fail_global(P3M_ECUDA, "graph capture: %s", cudaGetErrorString(err));
-    err = cudaEventRecord(e->fork, e->parent);
     int rc = P3M_OK;
-    for (int i = 0; i < e->n && err == cudaSuccess && rc == P3M_OK; ++i) {
-        c = e->c[i];
-        err = cudaStreamWaitEvent(c->stream, e->fork, 0);
-        if (err != cudaSuccess) break;
-        c->capturing = true;
-        for (int k = 0; k < steps && rc == P3M_OK; ++k) rc = step_body(c, 0.0, 0.0, true);
-        c->capturing = false;
-        if (rc == P3M_OK) err = cudaEventRecord(e->join[i], c->stream);
-        if (err == cudaSuccess && rc == P3M_OK) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
+    if (e->batched) {  // the steps one after another, each with its batched pair launch
+        for (int i = 0; i < e->n; ++i) e->c[i]->capturing = true;
+        for (int k = 0; k < steps && rc == P3M_OK; ++k) rc = ens_step(e, 0.0, 0.0, true);
+        for (int i = 0; i < e->n; ++i) e->c[i]->capturing = false;
+    } else {  // each context's steps as one branch
+        err = cudaEventRecord(e->fork, e->parent);
+        for (int i = 0; i < e->n && err == cudaSuccess && rc == P3M_OK; ++i) {
+            c = e->c[i];
+            err = cudaStreamWaitEvent(c->stream, e->fork, 0);
+            if (err != cudaSuccess) break;
+            c->capturing = true;
+            for (int k = 0; k < steps && rc == P3M_OK; ++k) rc = step_body(c, 0.0, 0.0, true);
+            c->capturing = false;
+            if (rc == P3M_OK) err = cudaEventRecord(e->join[i], c->stream);
+            if (err == cudaSuccess && rc == P3M_OK) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
+        }
     }
     cudaError_t end = cudaStreamEndCapture(e->parent, &graph);
     if (rc != P3M_OK) {
         if (graph) cudaGraphDestroy(graph);
-        return p3m_fail_global(rc, "graph capture: %s", c ? c->err : "step failed");
+        return p3m_fail_global(rc, "graph capture: %s", c ? c->err : g_init_err);
     }
     if (err == cudaSuccess) err = end;
     if (err == cudaSuccess) err = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (err != cudaSuccess)
         return p3m_fail_global(P3M_ECUDA, "graph capture: %s", cudaGetErrorString(err));
+    return P3M_OK;
+}
+
+// One step of every context with the batched pair launch: the contexts' pre-pair phases as
+// parallel branches (fork/join on the parent stream), then on the parent the merged work
+// list's total, its 16-bit cost sort and one pair kernel over all of them, then the energy
+// bookkeeping of contexts that track it.  from_table: graph-replayed (factors on the device).
+int ens_step(p3m_ensemble *e, double a, double da, bool from_table)
+{
+    cudaError_t err = cudaEventRecord(e->fork, e->parent);
+    int rc = P3M_OK;
+    for (int i = 0; i < e->n && err == cudaSuccess && rc == P3M_OK; ++i) {
+        p3m_ctx *c = e->c[i];
+        err = cudaStreamWaitEvent(c->stream, e->fork, 0);
+        if (err != cudaSuccess) break;
+        const int sl = e->slot[i];
+        rc = sl < 0 ? step_body(c, a, da, from_table)
+                    : step_pre(c, a, da, from_table, sl, e->descs + sl, e->gkey[0] + e->base[sl],
+                               e->gval[0] + e->base[sl]);
+        if (rc == P3M_OK) err = cudaEventRecord(e->join[i], c->stream);
+        if (err == cudaSuccess && rc == P3M_OK) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
+    }
+    if (rc != P3M_OK) {
+        for (int i = 0; i < e->n; ++i)
+            if (e->c[i]->err[0]) return p3m_fail_global(rc, "ensemble step: %s", e->c[i]->err);
+        return p3m_fail_global(rc, "ensemble step failed");
+    }
+    if (err == cudaSuccess) err = launch_ens_total(e->nwork, e->nb, e->gtotal, e->parent);
+    if (err == cudaSuccess) {
+        uint32_t *k[2] = {e->gkey[0], e->gkey[1]}, *v[2] = {e->gval[0], e->gval[1]};
+        err = radix_sort_pairs(k, v, false, (int64_t)e->cap, 16, e->gcounts, e->gaux, e->parent,
+                               &e->launches);
+        // two 8-bit passes: the result is back in gkey[0] / gval[0]
+        if (err == cudaSuccess && (k[0] != e->gkey[0] || v[0] != e->gval[0])) err = cudaErrorUnknown;
+    }
+    if (err == cudaSuccess)
+        err = launch_pairs_batched(e->descs, e->gval[0], e->gtotal, e->gcursor, e->c[0]->num_sms,
+                                   e->parent);
+    e->launches += 2;
+    bool tracking = false;
+    for (int i = 0; i < e->n; ++i) tracking = tracking || (e->slot[i] >= 0 && e->c[i]->track_energy);
+    if (err == cudaSuccess && tracking) {
+        err = cudaEventRecord(e->after_pairs, e->parent);
+        for (int i = 0; i < e->n && err == cudaSuccess; ++i) {
+            p3m_ctx *c = e->c[i];
+            if (e->slot[i] < 0 || !c->track_energy) continue;
+            err = cudaStreamWaitEvent(c->stream, e->after_pairs, 0);
+            if (err == cudaSuccess)
+                err = launch_li_update(c, from_table ? c->cur_fac + 3 : nullptr, a + da);
+            if (err == cudaSuccess) err = cudaEventRecord(e->join[i], c->stream);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
+        }
+    }
+    if (err != cudaSuccess)
+        return p3m_fail_global(P3M_ECUDA, "ensemble step: %s", cudaGetErrorString(err));
     return P3M_OK;
 }
 
@@ -1004,7 +1109,55 @@ extern "C" int p3m_ensemble_create(p3m_ensemble **out, p3m_ctx *const *ctxs, int
         p3m_ensemble_free(e);
         return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_create: %s", cudaGetErrorString(err));
     }
+    // batched pair launch over the FP32 P3M contexts (work items coded (slot << 24) | item)
+    e->slot = (int *)malloc(sizeof(int) * n);
+    e->base = (size_t *)calloc(n, sizeof(size_t));
+    if (!e->slot || !e->base) err = cudaErrorMemoryAllocation;
+    std::vector<const uint32_t *> nw;
+    for (int i = 0; i < n && err == cudaSuccess; ++i) {
+        p3m_ctx *c = ctxs[i];
+        const bool ok = c->precision == P3M_PREC_MIXED && c->short_range &&
+                        c->max_work < (1u << 24) && e->nb < 255;
+        e->slot[i] = ok ? e->nb : -1;
+        if (ok) {
+            e->base[e->nb] = e->cap;
+            e->cap += c->max_work;
+            nw.push_back(c->work_off + c->g.n_cells);
+            ++e->nb;
+        }
+    }
+    if (err == cudaSuccess && e->nb > 0) {
+        const size_t tiles = (e->cap + P3M_SORT_TILE - 1) / P3M_SORT_TILE;
+        const size_t scan_n = 256 * tiles;
+        err = cudaMalloc((void **)&e->descs, sizeof(PairArgs) * e->nb);
+        if (err == cudaSuccess) err = cudaMalloc((void **)&e->nwork, sizeof(uint32_t *) * e->nb);
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b) {
+            err = cudaMalloc((void **)&e->gkey[b], 4 * e->cap);
+            if (err == cudaSuccess) err = cudaMalloc((void **)&e->gval[b], 4 * e->cap);
+        }
+        if (err == cudaSuccess) err = cudaMalloc((void **)&e->gcounts, 4 * 256 * tiles);
+        if (err == cudaSuccess) err = cudaMalloc((void **)&e->gaux, 4 * (scan_n / P3M_SORT_TILE + 4));
+        if (err == cudaSuccess) err = cudaMalloc((void **)&e->gtotal, 16);
+        if (err == cudaSuccess) err = cudaMalloc((void **)&e->gcursor, 16);
+        if (err == cudaSuccess)
+            err = cudaMemcpy((void *)e->nwork, nw.data(), sizeof(uint32_t *) * e->nb, cudaMemcpyHostToDevice);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->after_pairs, cudaEventDisableTiming);
+    }
+    e->batched = false;  // measured slower than per-context branches on uneven ensembles
+    if (err != cudaSuccess) {
+        p3m_ensemble_free(e);
+        return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_create: %s", cudaGetErrorString(err));
+    }
     *out = e;
+    return P3M_OK;
+}
+
+extern "C" int p3m_ensemble_set_batched(p3m_ensemble *e, int enable)
+{
+    if (!e) return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_set_batched: NULL ensemble");
+    const bool want = enable && e->nb >= 1;
+    if (want != e->batched) drop_graphs(e);
+    e->batched = want;
     return P3M_OK;
 }
 
@@ -1029,7 +1182,18 @@ extern "C" int p3m_ensemble_run(p3m_ensemble *e, const double *a_list, int n_ste
             c->forces_valid = true;
         }
     }
-    if (!use_graph) {
+    if (!use_graph && e->batched) {
+        for (int k = 0; k < n_steps; ++k) {
+            int rc = ens_step(e, a_list[k], a_list[k + 1] - a_list[k], false);
+            if (rc) return rc;
+        }
+        // later work on the contexts' own streams comes after the last batched launch
+        cudaError_t err = cudaEventRecord(e->fork, e->parent);
+        for (int i = 0; i < e->n && err == cudaSuccess; ++i)
+            err = cudaStreamWaitEvent(e->c[i]->stream, e->fork, 0);
+        if (err != cudaSuccess)
+            return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_run: %s", cudaGetErrorString(err));
+    } else if (!use_graph) {
         for (int k = 0; k < n_steps; ++k)
             for (int i = 0; i < e->n; ++i) {
                 int rc = step_body(e->c[i], a_list[k], a_list[k + 1] - a_list[k], false);
@@ -1127,6 +1291,13 @@ extern "C" void p3m_ensemble_free(p3m_ensemble *e)
         if (e->join && e->join[i]) cudaEventDestroy(e->join[i]);
     }
     if (e->fork) cudaEventDestroy(e->fork);
+    if (e->after_pairs) cudaEventDestroy(e->after_pairs);
+    void *dbufs[] = {e->descs, (void *)e->nwork, e->gkey[0], e->gkey[1], e->gval[0], e->gval[1],
+                     e->gcounts,  e->gaux, e->gtotal, e->gcursor};
+    for (void *q : dbufs)
+        if (q) cudaFree(q);
+    free(e->slot);
+    free(e->base);
     if (e->parent) cudaStreamDestroy(e->parent);
     free(e->c);
     free(e->join);

@@ -136,6 +136,29 @@ enum {
 #define P3M_PAIR_TJ 128      // j-particles per shared-memory tile (4 blocks of 32)
 #define P3M_FLAG_TIMEOUT 1u  // counters[1] bit: a bounded wait gave up
 
+// Everything the FP32 pair kernel needs from one context: its arrays, geometry, fitted split
+// factor and culling radii, where the accelerations go and the fused final half-kick (factor
+// kfac, or *kfac_dev when that is set).  Passed by value for one context, or as a device array
+// indexed by simulation in the batched ensemble launch.
+struct PairArgs {
+    const float *relx;
+    const float4 *rel;
+    const double *pos;
+    const float4 *block_box;
+    const uint32_t *cell_start;
+    const uint32_t *work;
+    const double *acc_in;
+    double *acc_out;
+    double *mom;
+    const double *kfac_dev;
+    uint32_t *counters;
+    unsigned long long *pair_count;
+    double kfac;
+    P3MGeom g;
+    float gpoly[12];
+    float rcull2, rin2;
+};
+
 // A neighbour cell of a pair work item, for the FP32 pair kernels: the shift between the two
 // cells' origins (periodic image included) as an FP32 value plus the FP32 residual of the FP64
 // shift, the periodic image alone, and the neighbour's range of sorted slots.
@@ -214,6 +237,26 @@ cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int 
 // ------------------------------------------------------------------ launchers (pair.cu)
 // acc_out = acc_in + SR (acc_in NULL: SR only); kfac != 0: mom += kfac * acc_out.  kfac_dev
 // (nullable): read kfac from device memory instead.
+// FP32 contexts: the pair kernel's arguments for the current buffers (host-side fill).
+PairArgs pair_args(const p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+                   const double *kfac_dev);
+// One pair launch over the work items of several FP32 contexts: order[k] = (sim << 24) | item,
+// sorted by cost; *n_total items; descs[sim] the contexts' arguments; cursor zeroed here.
+cudaError_t launch_pairs_batched(const PairArgs *descs, const uint32_t *order,
+                                 const uint32_t *n_total, uint32_t *cursor, int num_sms,
+                                 cudaStream_t s);
+// dst (device) = a, as one kernel (so that captured graphs write the current pointers).
+cudaError_t launch_store_pair_args(PairArgs *dst, const PairArgs &a, cudaStream_t s);
+// Batched launch bookkeeping: copies one context's sorted work list (n entries) into the merged
+// arrays, values coded (slot << 24) | item; *total = sum over nb contexts of *nwork[k].
+cudaError_t launch_ens_gather(int slot, const uint32_t *key, const uint32_t *order, size_t n,
+                              uint32_t *gkey, uint32_t *gval, cudaStream_t s);
+cudaError_t launch_ens_total(const uint32_t *const *nwork, int nb, uint32_t *total, cudaStream_t s);
+// Stable LSD radix sort of n (key, value) pairs on the low key_bits bits; k[0]/v[0] hold the
+// result on return (the arrays are swapped when an odd number of passes ran).
+cudaError_t radix_sort_pairs(uint32_t **k, uint32_t **v, bool identity_vals, int64_t n,
+                             int key_bits, uint32_t *counts, uint32_t *aux, cudaStream_t s,
+                             unsigned long long *launches);
 cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
                          const double *kfac_dev = nullptr);
 

@@ -24,6 +24,8 @@
 // and evaluates g with erfc/exp.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "p3m_internal.cuh"
 
 namespace {
@@ -455,37 +457,43 @@ __device__ __forceinline__ f2 pair_factor2(f2 r2, const PairConst2 &k)
     return f2_mul(gval, f2_mul(f2_mul(s, s), s));
 }
 
-__global__ void __launch_bounds__(32)
-    k_pairs_x2(const float *__restrict__ relx, const float4 *__restrict__ rel,
-               const double *__restrict__ pos, const float4 *__restrict__ block_box,
-               const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ work,
-               const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_work_ptr,
-               P3MGeom g, GPoly gp, float rcull2, float rin2, const double *__restrict__ acc_in,
-               double *__restrict__ acc_out, double *__restrict__ mom, double kfac,
-               const double *__restrict__ kfac_dev, uint32_t *__restrict__ counters,
-               unsigned long long *__restrict__ pair_count)
+template <bool kBatched>
+__global__ void __launch_bounds__(32, 32)
+    k_pairs_x2(PairArgs a0, const PairArgs *__restrict__ descs, const uint32_t *__restrict__ order,
+               const uint32_t *__restrict__ n_work_ptr, uint32_t *__restrict__ cursor)
 {
     constexpr int kBlockFloats = 96;  // x[32] y[32] z[32]
-    if (kfac_dev) kfac = *kfac_dev;
+    constexpr int kArgWords = sizeof(PairArgs) / 8;
+    static_assert(sizeof(PairArgs) % 8 == 0, "PairArgs is copied in 8-byte words");
     __shared__ __align__(128) float sj[2][kBlocksPerTileX2 * kBlockFloats];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ NeighbourF nbr[27];
+    __shared__ __align__(16) PairArgs sA;  // the current work item's context
+    const PairArgs &A = sA;
 
     const int lane = threadIdx.x;
-    const int64_t n = g.n;
-    const int64_t nblocks = (n + 31) >> 5;
     const uint32_t n_work = *n_work_ptr;
-    const float rc2 = (float)(g.r_c * g.r_c);
-    const int nc = g.n_c;
+    int cur_sim = -1;
+    double kfac = 0.0;
     PairConst2 kc;
-#pragma unroll
-    for (int q = 0; q <= P3M_SPLIT_DEG; ++q) kc.c[q] = f2_pack(gp.c[q], gp.c[q]);
-    kc.c11 = f2_pack(gp.c[11], gp.c[11]);
     kc.m1 = f2_pack(-1.0f, -1.0f);
     kc.one = f2_pack(1.0f, 1.0f);
-    const float eps2 = (float)(g.eps * g.eps);
-    kc.eps2 = f2_pack(eps2, eps2);
     kc.tiny = f2_pack(kTiny, kTiny);
+    // (re)load the context's arguments into shared memory and the per-lane constants
+    auto load_args = [&](const PairArgs *src) {
+        __syncwarp();  // every lane is done with the previous arguments
+        const uint64_t *from = (const uint64_t *)src;
+        uint64_t *to = (uint64_t *)&sA;
+        for (int w = lane; w < kArgWords; w += 32) to[w] = from[w];
+        __syncwarp();
+        kfac = A.kfac_dev ? *A.kfac_dev : A.kfac;
+#pragma unroll
+        for (int q = 0; q <= P3M_SPLIT_DEG; ++q) kc.c[q] = f2_pack(A.gpoly[q], A.gpoly[q]);
+        kc.c11 = f2_pack(A.gpoly[11], A.gpoly[11]);
+        const float e2 = (float)(A.g.eps * A.g.eps);
+        kc.eps2 = f2_pack(e2, e2);
+    };
+    if (!kBatched) load_args(&a0);
 
     if (lane == 0) {
         mbar_init(&bar[0], 1);
@@ -494,29 +502,45 @@ __global__ void __launch_bounds__(32)
     }
     __syncwarp();
     uint32_t parity = 0u;
-    unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0, st_culled = 0,
-                       st_tiles = 0, st_empty_tiles = 0;
     bool timed_out = false;
 
     for (;;) {
         uint32_t slot = 0;
-        if (lane == 0) slot = atomicAdd(&counters[0], 1u);
+        if (lane == 0) slot = atomicAdd(cursor, 1u);
         slot = __shfl_sync(0xffffffffu, slot, 0);
         if (slot >= n_work) break;
-        const uint32_t item = order[slot];
-        const uint32_t cell = work[2 * (size_t)item];
-        const uint32_t first = work[2 * (size_t)item + 1];
-        const uint32_t cend = cell_start[cell + 1];
+        uint32_t item = order[slot];
+        if (kBatched) {
+            const int sim = (int)(item >> 24);
+            item &= 0xFFFFFFu;
+            if (sim != cur_sim) {
+                load_args(descs + sim);
+                cur_sim = sim;
+            }
+        }
+        const P3MGeom &g = A.g;
+        const int64_t n = g.n;
+        const int nc = g.n_c;
+        const float rc2 = (float)(g.r_c * g.r_c), rcull2 = A.rcull2, rin2 = A.rin2;
+        const float *__restrict__ relx = A.relx;
+        const float4 *__restrict__ block_box = A.block_box;
+        const uint32_t cell = A.work[2 * (size_t)item];
+        const uint32_t first = A.work[2 * (size_t)item + 1];
+        const uint32_t cend = A.cell_start[cell + 1];
         const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
-        if (lane < 27) nbr[lane] = make_neighbour(g, cell_start, cx, cy, cz, lane);
+        __syncwarp();  // the previous item is done with nbr
+        if (lane < 27) nbr[lane] = make_neighbour(g, A.cell_start, cx, cy, cz, lane);
         __syncwarp();
+        unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0, st_culled = 0,
+                           st_tiles = 0, st_empty_tiles = 0;
 
         const uint32_t i = first + lane;
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
-        const float4 xi = rel[ii];
+        const float4 xi = A.rel[ii];
         // absolute position in FP32, for the bounding-box tests only (their margins cover
         // the FP32 rounding of coordinates up to the box size)
+        const double *__restrict__ pos = A.pos;
         const float xa = (float)pos[ii], ya = (float)pos[n + ii], za = (float)pos[2 * n + ii];
         float sax = 0.0f, say = 0.0f, saz = 0.0f, cax = 0.0f, cay = 0.0f, caz = 0.0f;
 
@@ -683,10 +707,16 @@ __global__ void __launch_bounds__(32)
             nb_c = nb_n;
             b_c = b_n;
         }
-        if (timed_out) break;
+        if (timed_out) {
+            if (lane == 0) atomicOr(&A.counters[1], P3M_FLAG_TIMEOUT);
+            break;
+        }
         if (valid) {
             const double a3[3] = {g.gm * ((double)sax + (double)cax), g.gm * ((double)say + (double)cay),
                                   g.gm * ((double)saz + (double)caz)};
+            const double *__restrict__ acc_in = A.acc_in;
+            double *__restrict__ acc_out = A.acc_out;
+            double *__restrict__ mom = A.mom;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double tot = (acc_in ? acc_in[d * n + i] : 0.0) + a3[d];
@@ -694,23 +724,22 @@ __global__ void __launch_bounds__(32)
                 if (kfac != 0.0) mom[d * n + i] = __dadd_rn(mom[d * n + i], __dmul_rn(kfac, tot));
             }
         }
-        __syncwarp();
-    }
-    (void)nblocks;
-    if (timed_out && lane == 0) atomicOr(&counters[1], P3M_FLAG_TIMEOUT);
+        // the item's pair count (warp sum) and work counters, into its context
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
-    if (lane == 0) {
-        if (my_pairs) {
-            atomicAdd(pair_count, my_pairs);
-            atomicAdd(pair_count + 1, my_pairs);
+        for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+        if (lane == 0) {
+            unsigned long long *pc = A.pair_count;
+            if (my_pairs) {
+                atomicAdd(pc, my_pairs);
+                atomicAdd(pc + 1, my_pairs);
+            }
+            if (st_fast) atomicAdd(pc + 2, st_fast);
+            if (st_tested) atomicAdd(pc + 3, st_tested);
+            if (st_eval) atomicAdd(pc + 4, 2 * st_eval);
+            if (st_culled) atomicAdd(pc + 5, st_culled);
+            if (st_tiles) atomicAdd(pc + 6, st_tiles);
+            if (st_empty_tiles) atomicAdd(pc + 7, st_empty_tiles);
         }
-        if (st_fast) atomicAdd(pair_count + 2, st_fast);
-        if (st_tested) atomicAdd(pair_count + 3, st_tested);
-        if (st_eval) atomicAdd(pair_count + 4, 2 * st_eval);
-        if (st_culled) atomicAdd(pair_count + 5, st_culled);
-        if (st_tiles) atomicAdd(pair_count + 6, st_tiles);
-        if (st_empty_tiles) atomicAdd(pair_count + 7, st_empty_tiles);
     }
 }
 
@@ -744,25 +773,105 @@ cudaError_t pairs_x2_impl(p3m_ctx *c, const double *acc_in, double *acc_out, dou
                           const double *kfac_dev)
 {
     cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
-    cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);  // last evaluation
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2, 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2<false>, 32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    GPoly gp;
-    for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
-    const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
-    const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
     c->launches += 1;
-    k_pairs_x2<<<c->num_sms * per_sm, 32, 0, c->stream>>>(
-        c->relx, (const float4 *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
-        c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
-        rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, kfac_dev,
-        c->counters, c->pair_count);
+    k_pairs_x2<false><<<c->num_sms * per_sm, 32, 0, c->stream>>>(
+        pair_args(c, acc_in, acc_out, kfac, kfac_dev), nullptr, c->work_order,
+        c->work_off + c->g.n_cells, c->counters);
     return cudaGetLastError();
 }
 
+__global__ void k_store_pair_args(PairArgs *dst, PairArgs a) { *dst = a; }
+
+__global__ void k_ens_gather(uint32_t slot, const uint32_t *__restrict__ key,
+                             const uint32_t *__restrict__ order, size_t n, uint32_t *__restrict__ gk,
+                             uint32_t *__restrict__ gv)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        gk[k] = key[k];
+        gv[k] = (slot << 24) | (order[k] & 0xFFFFFFu);
+    }
+}
+
+__global__ void k_ens_total(const uint32_t *const *nwork, int nb, uint32_t *total)
+{
+    uint32_t t = 0;
+    for (int k = 0; k < nb; ++k) t += *nwork[k];
+    *total = t;
+}
+
 }  // namespace
+
+PairArgs pair_args(const p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+                   const double *kfac_dev)
+{
+    PairArgs a;
+    memset(&a, 0, sizeof(a));
+    a.relx = c->relx;
+    a.rel = (const float4 *)c->rel;
+    a.pos = c->pos;
+    a.block_box = c->block_box;
+    a.cell_start = c->cell_start;
+    a.work = c->work;
+    a.acc_in = acc_in;
+    a.acc_out = acc_out;
+    a.mom = c->mom;
+    a.kfac_dev = kfac_dev;
+    a.counters = c->counters;
+    a.pair_count = c->pair_count;
+    a.kfac = kfac;
+    a.g = c->g;
+    for (int k = 0; k < 12; ++k) a.gpoly[k] = c->gpoly[k];
+    // culling radii: r_c widened (narrowed) by more than the FP32 rounding of absolute
+    // coordinates up to the box size
+    const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
+    const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
+    a.rcull2 = (float)(rcull * rcull);
+    a.rin2 = rin > 0.0 ? (float)(rin * rin) : 0.0f;
+    return a;
+}
+
+cudaError_t launch_pairs_batched(const PairArgs *descs, const uint32_t *order,
+                                 const uint32_t *n_total, uint32_t *cursor, int num_sms,
+                                 cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2<true>, 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    PairArgs unused;
+    memset(&unused, 0, sizeof(unused));
+    k_pairs_x2<true><<<num_sms * per_sm, 32, 0, s>>>(unused, descs, order, n_total, cursor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_pair_args(PairArgs *dst, const PairArgs &a, cudaStream_t s)
+{
+    k_store_pair_args<<<1, 1, 0, s>>>(dst, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ens_gather(int slot, const uint32_t *key, const uint32_t *order, size_t n,
+                              uint32_t *gkey, uint32_t *gval, cudaStream_t s)
+{
+    const size_t blocks = (n + 255) / 256;
+    k_ens_gather<<<(unsigned)(blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks)), 256, 0, s>>>(
+        (uint32_t)slot, key, order, n, gkey, gval);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ens_total(const uint32_t *const *nwork, int nb, uint32_t *total, cudaStream_t s)
+{
+    k_ens_total<<<1, 1, 0, s>>>(nwork, nb, total);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
                          const double *kfac_dev)

@@ -45,6 +45,13 @@ def _case(name):
     if name == "random5003":  # N not a cube, ragged tiles everywhere
         pos = S.uniform_random(5003, 80.0, 77)
         return pos, np.zeros_like(pos), dict(box=80.0, mesh=40)
+    if name == "nc3":  # the smallest chaining mesh: 3 cells per side, every cell a neighbour
+        pos = S.uniform_random(2000, 64.0, 91)
+        return pos, np.zeros_like(pos), dict(box=64.0, mesh=20)
+    if name == "coincident":  # 200 exact duplicates: r = 0 pairs add nothing and are not counted
+        base = S.uniform_random(600, 40.0, 92)
+        pos = np.concatenate([base, base[:, :200]], axis=1)
+        return pos, np.zeros_like(pos), dict(box=40.0, mesh=32)
     if name == "tiny3":
         pos = np.array([[1.0, 1.5, 30.0], [2.0, 2.0, 31.0], [3.0, 3.3, 0.5]])
         return pos, np.zeros_like(pos), dict(box=32.0, mesh=32)
@@ -122,7 +129,8 @@ def test_density_mesh(P3M, precision):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-@pytest.mark.parametrize("case", ["eds32", "clustered48", "random5003", "tiny3"])
+@pytest.mark.parametrize("case", ["eds32", "clustered48", "random5003", "tiny3", "nc3",
+                                  "coincident"])
 def test_force_parts_match_oracle(P3M, case, precision):
     pos, mom, kw = _case(case)
     n = pos.shape[1]
