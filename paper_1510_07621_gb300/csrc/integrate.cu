@@ -24,7 +24,7 @@ __global__ void k_kick(double *__restrict__ mom, const double *__restrict__ acc,
 
 __device__ __forceinline__ double wrap_box(double x, double L)
 {
-    x = fmod(x, L);
+    if (!(x > -L && x < L)) x = fmod(x, L);  // fmod(x, L) == x exactly for -L < x < L
     if (x < 0.0) x = __dadd_rn(x, L);
     if (x >= L) x = __dadd_rn(x, -L);
     return x;

@@ -107,18 +107,42 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < per; ++r) {
-            if (!act[r]) continue;
+            // the warp's 32 particles are consecutive in the sorted order; lanes whose base
+            // nodes agree form runs of consecutive lanes
             const int lx = i0[r][0] - blo[0], ly = i0[r][1] - blo[1], lz = i0[r][2] - blo[2];
+            const int key = act[r] ? (lx * bdim[1] + ly) * bdim[2] + lz : -1 - lane;
+            const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+            const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
             const T wx[2] = {T(1) - f[r][0], f[r][0]}, wy[2] = {T(1) - f[r][1], f[r][1]};
             const T wz[2] = {T(1) - f[r][2], f[r][2]};
+            T w[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) w[c] = wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1];
+            if (__popc(heads) <= 8) {
+                // few runs (dense region): each run's weights summed onto its first lane by a
+                // segmented reduction, then one set of 8 shared-memory atomics per run
+                const int rid = __popc(heads & ((2u << lane) - 1u));
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int rid_o = __shfl_down_sync(0xffffffffu, rid, off);
+                    const bool same = lane + off < 32 && rid_o == rid;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const T o = __shfl_down_sync(0xffffffffu, w[c], off);
+                        if (same) w[c] += o;
+                    }
+                }
+                if (!(act[r] && ((heads >> lane) & 1u))) continue;
+            } else if (!act[r]) {
+                continue;
+            }
 #pragma unroll
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    const T wab = wx[a] * wy[b];
                     T *row = tile + ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
-                    atomicAdd(row, wab * wz[0]);
-                    atomicAdd(row + 1, wab * wz[1]);
+                    atomicAdd(row, w[(a << 2) | (b << 1)]);
+                    atomicAdd(row + 1, w[(a << 2) | (b << 1) | 1]);
                 }
         }
         __syncthreads();

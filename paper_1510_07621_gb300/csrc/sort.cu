@@ -25,7 +25,9 @@ constexpr int kRadix = 1 << kRadixBits;
 
 __device__ __forceinline__ double wrap_box(double x, double L)
 {
-    x = fmod(x, L);
+    // fmod(x, L) == x exactly for -L < x < L, so it only runs for far-out positions (it is a
+    // long FP64 sequence, and GB300's FP64 rate is low)
+    if (!(x > -L && x < L)) x = fmod(x, L);
     if (x < 0.0) x = __dadd_rn(x, L);
     if (x >= L) x = __dadd_rn(x, -L);
     return x;
