@@ -239,7 +239,7 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table = fal
     c->sorted_valid = true;
     {
         Phase ph(c, PH_DEPOSIT);
-        CK(launch_deposit(c));
+        CK(launch_deposit(c, true));
     }
     {
         Phase ph(c, PH_FFT_R2C);

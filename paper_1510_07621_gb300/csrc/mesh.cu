@@ -38,6 +38,29 @@ __device__ __forceinline__ void cic_stencil(double x, double inv_h, int &i0, T &
     f = (T)(u - fl);
 }
 
+// CIC stencil of a sorted particle in FP32 from its cell-relative coordinates (FP32 mode).  The
+// node coordinate is u = c M/n_c + rel M/L for cell coordinate c; c M = q n_c + r is split in
+// integers, so only v = r/n_c + rel M/L (below 1 + M/n_c) is rounded to FP32: i0 = q + floor(v),
+// f = v - floor(v).  CIC weights are continuous across node planes, so a rounding that moves
+// floor(v) by one at a plane changes the weights by the same rounding only.
+__device__ __forceinline__ void cic_stencil_rel(const float4 rv, uint32_t cell, const P3MGeom &g,
+                                                float inv_h, float inv_nc, int i0[3], float f[3])
+{
+    const int nc = g.n_c, M = g.mesh;
+    const int cc[3] = {(int)(cell % (uint32_t)nc), (int)((cell / (uint32_t)nc) % (uint32_t)nc),
+                       (int)(cell / (uint32_t)(nc * nc))};
+    const float rr[3] = {rv.x, rv.y, rv.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int cm = cc[d] * M;
+        const int q = cm / nc, r = cm - q * nc;
+        const float v = fmaf(rr[d], inv_h, (float)r * inv_nc);
+        const float fl = floorf(v);
+        i0[d] = q + (int)fl;
+        f[d] = v - fl;
+    }
+}
+
 // Fixed-size chunks of the sorted particles (CTA b takes slots [b*1024, (b+1)*1024)), so that a
 // dense cell is spread over many CTAs.  The chunk's CIC nodes are accumulated in a shared-memory
 // tile spanning the chunk's node bounding box (found by a block reduction); the tile is then
@@ -48,8 +71,12 @@ constexpr int kDepTileMax = 4096;  // nodes
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_deposit_chunks(const double *__restrict__ pos, P3MGeom g, T *__restrict__ mesh)
+    k_deposit_chunks(const double *__restrict__ pos, const float4 *__restrict__ rel,
+                     const uint32_t *__restrict__ keys, P3MGeom g, T *__restrict__ mesh)
 {
+    // rel != nullptr (FP32 mode, sorted state fresh): FP32 stencils from rel and the keys' cells
+    const float inv_h_f = (float)g.inv_h, inv_nc = 1.0f / (float)g.n_c;
+    const int csh = 3 * g.sub_bits;
     __shared__ T tile[kDepTileMax];
     __shared__ int s_lo[3][8], s_hi[3][8];
     const int M = g.mesh;
@@ -64,10 +91,20 @@ __global__ void __launch_bounds__(256)
     for (int r = 0; r < per; ++r) {
         const int64_t k = base + r * 256 + threadIdx.x;
         act[r] = k < n;
+        if (act[r] && sizeof(T) == 4 && rel) {
+            int ii[3];
+            float ff[3];
+            cic_stencil_rel(rel[k], keys[k] >> csh, g, inv_h_f, inv_nc, ii, ff);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                i0[r][d] = ii[d];
+                f[r][d] = (T)ff[d];
+            }
+        }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             if (act[r]) {
-                cic_stencil(pos[d * n + k], g.inv_h, i0[r][d], f[r][d]);
+                if (!(sizeof(T) == 4 && rel)) cic_stencil(pos[d * n + k], g.inv_h, i0[r][d], f[r][d]);
                 lo[d] = min(lo[d], i0[r][d]);
                 hi[d] = max(hi[d], i0[r][d] + 1);
             } else {
@@ -210,18 +247,33 @@ __global__ void __launch_bounds__(256)
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_gather(const double *__restrict__ pos, P3MGeom g, const T *__restrict__ fxm,
+    k_gather(const double *__restrict__ pos, const float4 *__restrict__ rel,
+             const uint32_t *__restrict__ keys, P3MGeom g, const T *__restrict__ fxm,
              const T *__restrict__ fym, const T *__restrict__ fzm, double *__restrict__ acc)
 {
     const int M = g.mesh;
     const int64_t n = g.n;
+    const float inv_h_f = (float)g.inv_h, inv_nc = 1.0f / (float)g.n_c;
+    const int csh = 3 * g.sub_bits;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int ix, iy, iz;
         T fx, fy, fz;
-        cic_stencil(pos[k], g.inv_h, ix, fx);
-        cic_stencil(pos[n + k], g.inv_h, iy, fy);
-        cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
+        if (sizeof(T) == 4 && rel) {  // FP32 mode: stencil from the cell-relative coordinates
+            int ii[3];
+            float ff[3];
+            cic_stencil_rel(rel[k], keys[k] >> csh, g, inv_h_f, inv_nc, ii, ff);
+            ix = ii[0];
+            iy = ii[1];
+            iz = ii[2];
+            fx = (T)ff[0];
+            fy = (T)ff[1];
+            fz = (T)ff[2];
+        } else {
+            cic_stencil(pos[k], g.inv_h, ix, fx);
+            cic_stencil(pos[n + k], g.inv_h, iy, fy);
+            cic_stencil(pos[2 * n + k], g.inv_h, iz, fz);
+        }
         const T wx[2] = {T(1) - fx, fx}, wy[2] = {T(1) - fy, fy}, wz[2] = {T(1) - fz, fz};
         const int jx[2] = {wrap_index(ix, M), wrap_index(ix + 1, M)};
         const int jy[2] = {wrap_index(iy, M), wrap_index(iy + 1, M)};
@@ -299,22 +351,24 @@ inline int grid_for(size_t n, int threads, int num_sms)
 }
 
 template <typename T>
-cudaError_t deposit_impl(p3m_ctx *c)
+cudaError_t deposit_impl(p3m_ctx *c, bool from_rel)
 {
     const size_t M3 = (size_t)c->g.mesh * c->g.mesh * c->g.mesh;
     T *mesh = (T *)c->rho;
     c->launches += 2;  // fill, deposit
     k_fill<T><<<grid_for(M3, 256, c->num_sms), 256, 0, c->stream>>>(mesh, M3, (T)(-c->g.mean_count));
     const int64_t chunks = (c->g.n + kDepChunk - 1) / kDepChunk;
-    k_deposit_chunks<T><<<(unsigned)chunks, 256, 0, c->stream>>>(c->pos, c->g, mesh);
+    k_deposit_chunks<T><<<(unsigned)chunks, 256, 0, c->stream>>>(
+        c->pos, from_rel && c->precision == P3M_PREC_MIXED ? (const float4 *)c->rel : nullptr,
+        c->keys, c->g, mesh);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_deposit(p3m_ctx *c)
+cudaError_t launch_deposit(p3m_ctx *c, bool from_rel)
 {
-    return c->precision == P3M_PREC_MIXED ? deposit_impl<float>(c) : deposit_impl<double>(c);
+    return c->precision == P3M_PREC_MIXED ? deposit_impl<float>(c, from_rel) : deposit_impl<double>(c, false);
 }
 
 cudaError_t launch_kspace(p3m_ctx *c)
@@ -364,10 +418,12 @@ cudaError_t launch_gather(p3m_ctx *c, double *acc_out)
     c->launches += 1;
     if (c->precision == P3M_PREC_MIXED) {
         const float *f = (const float *)c->frc;
-        k_gather<float><<<grid, 256, 0, c->stream>>>(c->pos, c->g, f, f + M3, f + 2 * M3, acc_out);
+        k_gather<float><<<grid, 256, 0, c->stream>>>(c->pos, (const float4 *)c->rel, c->keys, c->g, f,
+                                                     f + M3, f + 2 * M3, acc_out);
     } else {
         const double *f = (const double *)c->frc;
-        k_gather<double><<<grid, 256, 0, c->stream>>>(c->pos, c->g, f, f + M3, f + 2 * M3, acc_out);
+        k_gather<double><<<grid, 256, 0, c->stream>>>(c->pos, nullptr, nullptr, c->g, f, f + M3,
+                                                      f + 2 * M3, acc_out);
     }
     return cudaGetLastError();
 }

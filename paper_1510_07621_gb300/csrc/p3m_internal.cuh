@@ -228,8 +228,11 @@ cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_
                             cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers (mesh.cu)
-cudaError_t launch_deposit(p3m_ctx *c);
+// from_rel: the sorted state is fresh (right after the permute), so the FP32 mode may take the
+// stencils from the cell-relative coordinates; otherwise (any particle order) from pos in FP64.
+cudaError_t launch_deposit(p3m_ctx *c, bool from_rel = false);
 cudaError_t launch_kspace(p3m_ctx *c);
+// Right after the permute: the FP32 mode reads the stencils from the sorted rel and keys.
 cudaError_t launch_gather(p3m_ctx *c, double *acc_out);
 // Bins the spectrum in c->rho_k into acc[3 n_bins + 1] (see k_powspec).
 cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc);
