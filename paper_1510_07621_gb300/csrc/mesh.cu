@@ -82,10 +82,10 @@ __global__ void __launch_bounds__(256)
     const int M = g.mesh;
     const int64_t n = g.n;
     const int64_t base = (int64_t)blockIdx.x * kDepChunk;
-    const int per = kDepChunk / 256;
-    int i0[4][3];
-    T f[4][3];
-    bool act[4];
+    constexpr int per = kDepChunk / 256;
+    int i0[per][3];
+    T f[per][3];
+    bool act[per];
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
 #pragma unroll
     for (int r = 0; r < per; ++r) {
