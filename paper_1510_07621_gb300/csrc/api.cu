@@ -188,6 +188,7 @@ void release(p3m_ctx *c)
                     c->tab_k,     c->tab_kg,   c->tab_g,        c->work_key, c->work_key_alt,
                     c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
                     c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac,
+                    c->tab_origin,
                     c->adj_u,     c->adj_vf,   c->adj_vs,       c->adj_out,  c->kself,
                     c->li,        c->relx};
     for (void *p : bufs)
@@ -538,6 +539,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->tab_k, real * M},   {(void **)&c->tab_kg, real * M},
             {(void **)&c->tab_g, real * M},   {(void **)&c->tab_invw2, 8 * M},
             {(void **)&c->tab_one, 8 * M},    {(void **)&c->ps_acc, 8 * (3 * (M / 2) + 1)},
+            {(void **)&c->tab_origin, 8 * (size_t)g.n_c},
             {(void **)&c->fac_table, 8 * 4 * (size_t)P3M_MAX_GRAPH_STEPS},
             {(void **)&c->step_idx, 16},      {(void **)&c->cur_fac, 32},
             {(void **)&c->kself, 8 * 27},     {(void **)&c->li, 8 * 4},
@@ -597,6 +599,10 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             }
             e = cudaMemcpy(c->tab_invw2, w2.data(), 8 * M, cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(c->tab_one, one.data(), 8 * M, cudaMemcpyHostToDevice);
+            std::vector<double> org(g.n_c);
+            for (int q = 0; q < g.n_c; ++q) org[q] = (double)q * g.cs;
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->tab_origin, org.data(), 8 * (size_t)g.n_c, cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
             rc = fail(nullptr, P3M_ECUDA, "p3m_init: table upload failed: %s", cudaGetErrorString(e));

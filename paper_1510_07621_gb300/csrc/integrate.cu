@@ -24,7 +24,11 @@ __global__ void k_kick(double *__restrict__ mom, const double *__restrict__ acc,
 
 __device__ __forceinline__ double wrap_box(double x, double L)
 {
-    if (!(x > -L && x < L)) x = fmod(x, L);  // fmod(x, L) == x exactly for -L < x < L
+    // x = fmod(x, L); x < 0 -> x += L; x >= L -> x -= L.  Inside [0, L) (the common case after
+    // a drift) every step leaves x unchanged, and fmod(x, L) == x for -L < x < L: the FP64
+    // sequence, slow on GB300's FP64 pipe, runs only for the rest.
+    if (x >= 0.0 && x < L) return x;
+    if (!(x > -L && x < L)) x = fmod(x, L);
     if (x < 0.0) x = __dadd_rn(x, L);
     if (x >= L) x = __dadd_rn(x, -L);
     return x;

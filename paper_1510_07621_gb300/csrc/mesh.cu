@@ -61,12 +61,12 @@ __device__ __forceinline__ void cic_stencil_rel(const float4 rv, uint32_t cell, 
     }
 }
 
-// Fixed-size chunks of the sorted particles (CTA b takes slots [b*1024, (b+1)*1024)), so that a
+// Fixed-size chunks of the sorted particles (CTA b takes slots [b*512, (b+1)*512)), so that a
 // dense cell is spread over many CTAs.  The chunk's CIC nodes are accumulated in a shared-memory
 // tile spanning the chunk's node bounding box (found by a block reduction); the tile is then
 // added to the mesh with one global atomic per non-zero node.  A chunk whose box exceeds the
 // tile capacity (e.g. one that straddles the periodic boundary) adds straight to the mesh.
-constexpr int kDepChunk = 1024;
+constexpr int kDepChunk = 512;
 constexpr int kDepTileMax = 4096;  // nodes
 
 template <typename T>

@@ -67,6 +67,7 @@ struct p3m_ctx {
     void *tab_k, *tab_kg, *tab_g;  // per-axis |k|, gradient k, Green factor (length M)
     double *tab_invw2;             // per-axis 1/sinc^4(k h/2) (FP64, length M)
     double *tab_one;               // M ones (no deconvolution)
+    double *tab_origin;            // n_c chaining-cell origins c * cs (FP64, correctly rounded)
     double *ps_acc;                // power spectrum partial sums (3 * (M/2) + 1)
     double green_const;
     float gpoly[12];  // FP32 split factor: g = 1 + r^3 Q(tau), Q = sum gpoly[k] tau^k

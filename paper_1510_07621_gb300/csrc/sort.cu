@@ -25,8 +25,10 @@ constexpr int kRadix = 1 << kRadixBits;
 
 __device__ __forceinline__ double wrap_box(double x, double L)
 {
-    // fmod(x, L) == x exactly for -L < x < L, so it only runs for far-out positions (it is a
-    // long FP64 sequence, and GB300's FP64 rate is low)
+    // x = fmod(x, L); x < 0 -> x += L; x >= L -> x -= L.  Inside [0, L) (the common case after
+    // a drift) every step leaves x unchanged, and fmod(x, L) == x for -L < x < L: the FP64
+    // sequence, slow on GB300's FP64 pipe, runs only for the rest.
+    if (x >= 0.0 && x < L) return x;
     if (!(x > -L && x < L)) x = fmod(x, L);
     if (x < 0.0) x = __dadd_rn(x, L);
     if (x >= L) x = __dadd_rn(x, -L);
@@ -255,15 +257,17 @@ __device__ __forceinline__ double4 make_rel<double4>(double x, double y, double 
 // FP32 mode: position minus its cell origin (no FP32 absolute coordinate).  FP64 mode: the
 // absolute position itself, so that the pair kernel forms x_j - x_i exactly like a plain
 // minimum-image difference.
+// (origin[c] = c * cs, a host table: the same correctly rounded products without the FP64
+// multiply and conversion per particle)
 template <typename R4>
 __device__ __forceinline__ R4 rel_coords(double x, double y, double z, uint32_t cx, uint32_t cy,
-                                         uint32_t cz, double cs)
+                                         uint32_t cz, const double *origin)
 {
-    return make_rel<R4>(x - (double)cx * cs, y - (double)cy * cs, z - (double)cz * cs);
+    return make_rel<R4>(x - __ldg(origin + cx), y - __ldg(origin + cy), z - __ldg(origin + cz));
 }
 template <>
 __device__ __forceinline__ double4 rel_coords<double4>(double x, double y, double z, uint32_t,
-                                                       uint32_t, uint32_t, double)
+                                                       uint32_t, uint32_t, const double *)
 {
     return make_double4(x, y, z, 0.0);
 }
@@ -274,7 +278,8 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
                           const double *__restrict__ mom, const uint32_t *__restrict__ pid,
                           double *__restrict__ pos_out, double *__restrict__ mom_out,
                           uint32_t *__restrict__ pid_out, R4 *__restrict__ rel,
-                          float4 *__restrict__ block_box, float *__restrict__ relx)
+                          float4 *__restrict__ block_box, float *__restrict__ relx,
+                          const double *__restrict__ origin)
 {
     // one warp per 32-slot block of the sorted order; the warp also writes the block's
     // bounding box (FP32, absolute coordinates, rounded outwards by the callers' margins)
@@ -300,7 +305,7 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
             const uint32_t cell = keys[k] >> (3 * g.sub_bits);
             const uint32_t cx = cell % g.n_c, cy = (cell / g.n_c) % g.n_c,
                            cz = cell / (g.n_c * g.n_c);
-            rv = rel_coords<R4>(x, y, z, cx, cy, cz, g.cs);
+            rv = rel_coords<R4>(x, y, z, cx, cy, cz, origin);
             rel[k] = rv;
         }
         if (relx) {  // block-SoA copy of the relative coordinates (zero past the end)
@@ -472,12 +477,13 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     if (c->precision == P3M_PREC_MIXED)
         k_permute<float4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                      c->pid, c->pos_alt, c->mom_alt, c->pid_alt,
-                                                     (float4 *)c->rel, c->block_box, c->relx);
+                                                     (float4 *)c->rel, c->block_box, c->relx,
+                                                     c->tab_origin);
     else
         k_permute<double4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                       c->pid, c->pos_alt, c->mom_alt,
                                                       c->pid_alt, (double4 *)c->rel, c->block_box,
-                                                      nullptr);
+                                                      nullptr, c->tab_origin);
     double *t = c->pos;
     c->pos = c->pos_alt;
     c->pos_alt = t;
