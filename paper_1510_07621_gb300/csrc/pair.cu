@@ -17,11 +17,13 @@
 // no lane accepts.  CTAs are persistent and take work items, most expensive first, from an
 // atomic cursor.  No CTA-wide barrier: warps never wait for each other.
 //
-// Precision: FP32 mode uses coordinates relative to each particle's own cell origin (FP32),
-// shifted per neighbour cell by the FP64 offset between the two cell origins, per-tile FP32
-// partial sums added into FP64 accumulators, and g from a fitted polynomial (below).  FP64 mode
-// keeps absolute coordinates (d = (x_j - x_i) + image, like a plain minimum-image difference)
-// and evaluates g with erfc/exp.
+// Two kernels share that traversal.  k_pairs_x2 (FP32 mode) uses coordinates relative to each
+// particle's own cell origin in FP32, shifted per neighbour cell by the difference of the two
+// cell origins (an FP32 value plus its FP32 residual), evaluates two j particles per lane with
+// packed f32x2 arithmetic and g from a fitted polynomial, and adds per-tile sums with FP32
+// TwoSum compensation; nothing in its tile loop uses the FP64 pipe.  k_pairs64 (FP64 mode) keeps
+// absolute coordinates (d = (x_j - x_i) + image, like a plain minimum-image difference) and
+// evaluates g with erfc/exp.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -33,17 +35,6 @@ namespace {
 constexpr int kTJ = P3M_PAIR_TJ;  // 128
 constexpr int kBlocksPerTile = kTJ / 32;
 constexpr int kBlocksPerTileX2 = 4;  // FP32 kernel: 128 j particles (1.5 KB) per tile
-
-template <typename T>
-struct Vec4;
-template <>
-struct Vec4<float> {
-    using type = float4;
-};
-template <>
-struct Vec4<double> {
-    using type = double4;
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -117,12 +108,6 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 
-// Coefficients of the FP32 split factor, fitted on the host for the context's cutoff:
-// g = 1 + r^3 sum_k c[k] tau^k (k = 0..P3M_SPLIT_DEG), tau = r^2 c[11] - 1.
-struct GPoly {
-    float c[12];
-};
-
 // g(r/r_s) (r^2 + eps^2)^-3/2 for one pair in FP64, g from erfc and exp.
 __device__ __forceinline__ double pair_factor64(double r2, double eps2, double inv_rs)
 {
@@ -132,44 +117,30 @@ __device__ __forceinline__ double pair_factor64(double r2, double eps2, double i
     return g * s * s * s;
 }
 
-template <typename T>
-__device__ __forceinline__ T pair_factor(T r2, T eps2, const GPoly &gp, double inv_rs);
-template <>
-__device__ __forceinline__ double pair_factor<double>(double r2, double eps2, const GPoly &,
-                                                      double inv_rs)
-{
-    return pair_factor64(r2, eps2, inv_rs);
-}
-
 struct Neighbour {
     uint32_t start, end;
-    double sx, sy, sz;     // FP32 mode: origin(neighbour) - origin(own cell), image included;
-                           // FP64 mode: the periodic image only
-    double imx, imy, imz;  // periodic image (both modes)
+    double imx, imy, imz;  // periodic image of the neighbour cell
 };
 
-template <typename T>
 __global__ void __launch_bounds__(32)
-    k_pairs(const typename Vec4<T>::type *__restrict__ rel, const double *__restrict__ pos,
+    k_pairs64(const double4 *__restrict__ rel, const double *__restrict__ pos,
             const float4 *__restrict__ block_box, const uint32_t *__restrict__ cell_start,
             const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
-            const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPoly gp, float rcull2, float rin2,
+            const uint32_t *__restrict__ n_work_ptr, P3MGeom g, float rcull2, float rin2,
             const double *__restrict__ acc_in, double *__restrict__ acc_out,
             double *__restrict__ mom, double kfac, const double *__restrict__ kfac_dev,
             uint32_t *__restrict__ counters, unsigned long long *__restrict__ pair_count)
 {
-    using V4 = typename Vec4<T>::type;
-    constexpr bool kAbsolute = sizeof(T) == 8;
     if (kfac_dev) kfac = *kfac_dev;  // graph-replayed steps read the factor from the device
-    __shared__ __align__(128) V4 sj[2][kTJ];
+    __shared__ __align__(128) double4 sj[2][kTJ];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ Neighbour nbr[27];
 
     const int lane = threadIdx.x;
     const int64_t n = g.n;
     const uint32_t n_work = *n_work_ptr;
-    const T rc2 = (T)(g.r_c * g.r_c);
-    const T eps2 = (T)(g.eps * g.eps);
+    const double rc2 = g.r_c * g.r_c;
+    const double eps2 = g.eps * g.eps;
     const double inv_rs = 1.0 / g.r_s;
     const int nc = g.n_c;
 
@@ -203,19 +174,10 @@ __global__ void __launch_bounds__(32)
             q.start = cell_start[nb];
             q.end = cell_start[nb + 1];
             if (q.start == q.end) q.start = q.end = 0;  // empty: the tile walk skips it
-            const double L = g.box, cs = g.cs;
+            const double L = g.box;
             q.imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
             q.imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
             q.imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
-            if (kAbsolute) {
-                q.sx = q.imx;
-                q.sy = q.imy;
-                q.sz = q.imz;
-            } else {
-                q.sx = ((double)wx * cs + q.imx) - (double)cx * cs;
-                q.sy = ((double)wy * cs + q.imy) - (double)cy * cs;
-                q.sz = ((double)wz * cs + q.imz) - (double)cz * cs;
-            }
             nbr[lane] = q;
         }
         __syncwarp();
@@ -223,7 +185,7 @@ __global__ void __launch_bounds__(32)
         const uint32_t i = first + lane;
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
-        const V4 xi = rel[ii];
+        const double4 xi = rel[ii];
         const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];  // absolute, FP64
         double ax = 0.0, ay = 0.0, az = 0.0;
 
@@ -239,7 +201,7 @@ __global__ void __launch_bounds__(32)
             const uint32_t bend = min(b + kBlocksPerTile, (nbr[nb].end + 31) >> 5);
             const uint32_t j0 = b * 32;
             const uint32_t j1 = min((uint32_t)n, bend * 32);
-            const uint32_t bytes = (j1 - j0) * (uint32_t)sizeof(V4);
+            const uint32_t bytes = (j1 - j0) * (uint32_t)sizeof(double4);
             mbar_expect_tx(&bar[to], bytes);
             bulk_load(&sj[to][0], rel + j0, bytes, &bar[to]);
         };
@@ -265,17 +227,13 @@ __global__ void __launch_bounds__(32)
                 break;
             }
             const Neighbour &q = nbr[nb_c];
-            // FP32: xs = x_i - shift, d = x_j - xs;  FP64: d = (x_j - x_i) + image
-            const T xs = kAbsolute ? (T)xi.x : (T)((double)xi.x - q.sx);
-            const T ys = kAbsolute ? (T)xi.y : (T)((double)xi.y - q.sy);
-            const T zs = kAbsolute ? (T)xi.z : (T)((double)xi.z - q.sz);
-            const T ix = kAbsolute ? (T)q.sx : T(0);
-            const T iy = kAbsolute ? (T)q.sy : T(0);
-            const T iz = kAbsolute ? (T)q.sz : T(0);
+            // d = (x_j - x_i) + image, like a plain minimum-image difference
+            const double xs = xi.x, ys = xi.y, zs = xi.z;
+            const double ix = q.imx, iy = q.imy, iz = q.imz;
             // particle i in the frame of the block boxes (absolute, image removed)
             const float cxs = (float)(xa - q.imx), cys = (float)(ya - q.imy), czs = (float)(za - q.imz);
-            const V4 *tile = sj[buf];
-            T px = 0, py = 0, pz = 0;
+            const double4 *tile = sj[buf];
+            double px = 0, py = 0, pz = 0;
             uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0, n_culled = 0;
             for (uint32_t b = b_c; b < bend; ++b) {
                 const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
@@ -298,17 +256,12 @@ __global__ void __launch_bounds__(32)
                     n_fast += j1 - j0;
 #pragma unroll 2
                     for (uint32_t j = j0; j < j1; ++j) {
-                        const V4 qj = tile[j];
-                        T dx = qj.x - xs, dy = qj.y - ys, dz = qj.z - zs;
-                        if (kAbsolute) {
-                            dx += ix;
-                            dy += iy;
-                            dz += iz;
-                        }
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        const bool in = valid && r2 > T(0);
-                        T f = pair_factor<T>(r2, eps2, gp, inv_rs);
-                        f = in ? f : T(0);
+                        const double4 qj = tile[j];
+                        const double dx = (qj.x - xs) + ix, dy = (qj.y - ys) + iy, dz = (qj.z - zs) + iz;
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        const bool in = valid && r2 > 0.0;
+                        double f = pair_factor64(r2, eps2, inv_rs);
+                        f = in ? f : 0.0;
                         px += f * dx;
                         py += f * dy;
                         pz += f * dz;
@@ -318,19 +271,14 @@ __global__ void __launch_bounds__(32)
                 }
                 n_tested += j1 - j0;
                 for (uint32_t j = j0; j < j1; ++j) {
-                    const V4 qj = tile[j];
-                    T dx = qj.x - xs, dy = qj.y - ys, dz = qj.z - zs;
-                    if (kAbsolute) {
-                        dx += ix;
-                        dy += iy;
-                        dz += iz;
-                    }
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    const bool in = valid && r2 < rc2 && r2 > T(0);
+                    const double4 qj = tile[j];
+                    const double dx = (qj.x - xs) + ix, dy = (qj.y - ys) + iy, dz = (qj.z - zs) + iz;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const bool in = valid && r2 < rc2 && r2 > 0.0;
                     if (!__any_sync(0xffffffffu, in)) continue;
                     ++n_eval;
-                    T f = pair_factor<T>(r2, eps2, gp, inv_rs);
-                    f = in ? f : T(0);
+                    double f = pair_factor64(r2, eps2, inv_rs);
+                    f = in ? f : 0.0;
                     px += f * dx;
                     py += f * dy;
                     pz += f * dz;
@@ -743,27 +691,24 @@ __global__ void __launch_bounds__(32, 32)
     }
 }
 
-template <typename T>
-cudaError_t pairs_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
+cudaError_t pairs64_impl(p3m_ctx *c, const double *acc_in, double *acc_out, double kfac,
                        const double *kfac_dev)
 {
     cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
     cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);  // last evaluation
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<T>, 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs64, 32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int grid = c->num_sms * per_sm;
-    GPoly gp;
-    for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
     // culling radii: r_c widened (narrowed) by more than the FP32 rounding of absolute
     // coordinates up to the box size
     const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
     const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
     c->launches += 1;
-    k_pairs<T><<<grid, 32, 0, c->stream>>>(
-        (const typename Vec4<T>::type *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
-        c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
+    k_pairs64<<<grid, 32, 0, c->stream>>>(
+        (const double4 *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
+        c->work_order, c->work_off + c->g.n_cells, c->g, (float)(rcull * rcull),
         rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, kfac_dev,
         c->counters, c->pair_count);
     return cudaGetLastError();
@@ -877,5 +822,5 @@ cudaError_t launch_pairs(p3m_ctx *c, const double *acc_in, double *acc_out, doub
                          const double *kfac_dev)
 {
     return c->precision == P3M_PREC_MIXED ? pairs_x2_impl(c, acc_in, acc_out, kfac, kfac_dev)
-                                          : pairs_impl<double>(c, acc_in, acc_out, kfac, kfac_dev);
+                                          : pairs64_impl(c, acc_in, acc_out, kfac, kfac_dev);
 }
