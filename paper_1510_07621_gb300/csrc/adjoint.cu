@@ -15,6 +15,7 @@
 
 #include <vector>
 
+#include "p3m_device.cuh"
 #include "p3m_internal.cuh"
 
 namespace {
@@ -44,7 +45,7 @@ __device__ __forceinline__ void stencil64(double x, double inv_h, int &i0, doubl
 
 // v_sorted[k] = v[pid[k]] (caller order -> slot order), also an FP32 copy with w = 0.
 __global__ void k_to_slots(const double *__restrict__ v, const uint32_t *__restrict__ pid,
-                           int64_t n, double *__restrict__ vs, float4 *__restrict__ vf)
+                           int64_t n, double *__restrict__ vs, float *__restrict__ vfx)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -53,7 +54,12 @@ __global__ void k_to_slots(const double *__restrict__ v, const uint32_t *__restr
         vs[k] = a;
         vs[n + k] = b;
         vs[2 * n + k] = c;
-        vf[k] = make_float4((float)a, (float)b, (float)c, 0.0f);
+        if (vfx) {  // FP32 block-SoA copy (per 32-slot block vx[32] vy[32] vz[32])
+            float *dst = vfx + (k >> 5) * 96 + (k & 31);
+            dst[0] = (float)a;
+            dst[32] = (float)b;
+            dst[64] = (float)c;
+        }
     }
 }
 
@@ -205,39 +211,14 @@ __global__ void k_sum_parts(double *part, int nb, double *out)
 
 // ------------------------------------------------------------------ pair part
 
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
+// Coefficients of the FP32 split factor (the context's fitted polynomial, see p3m_ctx::gpoly).
 struct GPolyA {
     float c[12];
 };
 
-// h(r)/Gm and h'(r)/(Gm r) for one pair (FP32): g from the fitted polynomial, g' in closed form.
-__device__ __forceinline__ void pair_jac(float r2, float eps2, float inv_rs, const GPolyA &gp,
-                                         float &h, float &hr)
-{
-    const float t = rsqrt_approx(r2);
-    const float s = rsqrt_approx(r2 + eps2);
-    const float r = r2 * t;
-    const float tau = fmaf(r2, gp.c[11], -1.0f);
-    float p = gp.c[P3M_SPLIT_DEG];
-#pragma unroll
-    for (int k = P3M_SPLIT_DEG - 1; k >= 0; --k) p = fmaf(p, tau, gp.c[k]);
-    const float gval = fmaf(r2 * r, p, 1.0f);
-    const float x = r * inv_rs;
-    const float gder = -x * x * __expf(-0.25f * x * x) * 0.282094791773878143f;  // 1/(2 sqrt pi)
-    const float s3 = s * s * s;
-    h = gval * s3;
-    // h' / r = [g'/r_s s^3 - 3 r g s^5] / r
-    hr = gder * inv_rs * s3 * t - 3.0f * gval * s3 * s * s;
-}
-
-__device__ __forceinline__ void pair_jac(double r2, double eps2, double inv_rs, const GPolyA &,
-                                         double &h, double &hr)
+// h(r)/Gm and h'(r)/(Gm r) for one pair in FP64, g and g' in closed form.
+__device__ __forceinline__ void pair_jac(double r2, double eps2, double inv_rs, double &h,
+                                         double &hr)
 {
     const double r = sqrt(r2), x = r * inv_rs;
     const double s2 = r2 + eps2, s3 = s2 * sqrt(s2);
@@ -258,27 +239,23 @@ struct V4Of<double> {
     using type = double4;
 };
 
-// One warp per work item (up to 32 particles of one cell, most expensive items first), like
-// the force pair kernel: the j particles of the 27 neighbour cells in 32-slot blocks, a block
-// skipped when no lane's particle is within r_c of its bounding box, evaluated without pair
-// tests when it lies within r_c of every lane's particle.  j data read through the cache.
-// out_k += Gm sum_j J(d_kj) (v_j - v_k).
-template <typename T>
+// FP64 mode: one warp per work item (up to 32 particles of one cell, most expensive items first),
+// like the force pair kernel: the j particles of the 27 neighbour cells in 32-slot blocks, a
+// block skipped when no lane's particle is within r_c of its bounding box, evaluated without
+// pair tests when it lies within r_c of every lane's particle; j data read through the cache
+// and broadcast by shuffles.  out_k += Gm sum_j J(d_kj) (v_j - v_k).
 __global__ void __launch_bounds__(32)
-    k_pairs_vjp(const typename V4Of<T>::type *__restrict__ rel, const double *__restrict__ pos,
-                const float4 *__restrict__ block_box, const float4 *__restrict__ vf,
-                const double *__restrict__ vs, const uint32_t *__restrict__ cell_start,
-                const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
-                const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPolyA gp, float rcull2,
-                float rin2, uint32_t *__restrict__ cursor, double *__restrict__ out)
+    k_pairs_vjp64(const double4 *__restrict__ rel, const double *__restrict__ pos,
+                  const float4 *__restrict__ block_box, const double *__restrict__ vs,
+                  const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ work,
+                  const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_work_ptr,
+                  P3MGeom g, float rcull2, float rin2, uint32_t *__restrict__ cursor,
+                  double *__restrict__ out)
 {
-    using V4 = typename V4Of<T>::type;
-    constexpr bool kAbsolute = sizeof(T) == 8;
-    __shared__ NeighbourF nbr[27];  // FP32 mode: the item's neighbours, FP32 shifts
     const int lane = threadIdx.x;
     const int64_t n = g.n;
     const uint32_t n_work = *n_work_ptr;
-    const T rc2 = (T)(g.r_c * g.r_c), eps2 = (T)(g.eps * g.eps), inv_rs = (T)(1.0 / g.r_s);
+    const double rc2 = g.r_c * g.r_c, eps2 = g.eps * g.eps, inv_rs = 1.0 / g.r_s;
     const int nc = g.n_c;
     for (;;) {
         uint32_t slot = 0;
@@ -289,57 +266,25 @@ __global__ void __launch_bounds__(32)
         const uint32_t cell = work[2 * (size_t)item], first = work[2 * (size_t)item + 1];
         const uint32_t cend = cell_start[cell + 1];
         const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
-        if (!kAbsolute) {
-            __syncwarp();  // the previous item is done with nbr
-            if (lane < 27) nbr[lane] = make_neighbour(g, cell_start, cx, cy, cz, lane);
-            __syncwarp();
-        }
         const uint32_t i = first + lane;
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
-        const V4 xi = rel[ii];
+        const double4 xi = rel[ii];
         const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];
-        const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za;
-        const T vix = (T)vs[ii], viy = (T)vs[n + ii], viz = (T)vs[2 * n + ii];
-        double o[3] = {0.0, 0.0, 0.0};             // FP64 mode
-        float so[3] = {0, 0, 0}, co[3] = {0, 0, 0};  // FP32 mode: TwoSum sum and compensation
+        const double vix = vs[ii], viy = vs[n + ii], viz = vs[2 * n + ii];
+        double o[3] = {0.0, 0.0, 0.0};
         for (int nb = 0; nb < 27; ++nb) {
-            uint32_t js, je;
-            T xs, ys, zs, ix = 0, iy = 0, iz = 0;
-            float cxs, cys, czs;
-            if (kAbsolute) {
-                const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
-                const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
-                const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
-                js = cell_start[q];
-                je = cell_start[q + 1];
-                if (js == je) continue;
-                const double L = g.box;
-                const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);
-                const double imy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
-                const double imz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
-                xs = (T)xi.x;
-                ys = (T)xi.y;
-                zs = (T)xi.z;
-                ix = (T)imx;
-                iy = (T)imy;
-                iz = (T)imz;
-                cxs = (float)(xa - imx);
-                cys = (float)(ya - imy);
-                czs = (float)(za - imz);
-            } else {
-                const NeighbourF &q = nbr[nb];
-                js = q.start;
-                je = q.end;
-                if (js == je) continue;
-                xs = (T)(((float)xi.x - q.sx) - q.rx);
-                ys = (T)(((float)xi.y - q.sy) - q.ry);
-                zs = (T)(((float)xi.z - q.sz) - q.rz);
-                cxs = xaf - q.imx;
-                cys = yaf - q.imy;
-                czs = zaf - q.imz;
-            }
-            T ox = 0, oy = 0, oz = 0;
+            const int ux = cx + nb % 3 - 1, uy = cy + (nb / 3) % 3 - 1, uz = cz + nb / 9 - 1;
+            const int wx = (ux + nc) % nc, wy = (uy + nc) % nc, wz = (uz + nc) % nc;
+            const uint32_t q = ((uint32_t)wz * nc + wy) * nc + wx;
+            const uint32_t js = cell_start[q], je = cell_start[q + 1];
+            if (js == je) continue;
+            const double L = g.box;
+            const double ix = ux < 0 ? -L : (ux >= nc ? L : 0.0);
+            const double iy = uy < 0 ? -L : (uy >= nc ? L : 0.0);
+            const double iz = uz < 0 ? -L : (uz >= nc ? L : 0.0);
+            const float cxs = (float)(xa - ix), cys = (float)(ya - iy), czs = (float)(za - iz);
+            double ox = 0, oy = 0, oz = 0;
             for (uint32_t b = js >> 5; b * 32u < je; ++b) {
                 const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
                 const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
@@ -354,62 +299,266 @@ __global__ void __launch_bounds__(32)
                 const uint32_t j0 = max(b * 32, js), j1 = min(b * 32 + 32, je);
                 // the block's particles: one coalesced load, then broadcast lane by lane
                 const uint32_t jl = min(b * 32 + lane, (uint32_t)(n - 1));
-                const V4 ql = rel[jl];
-                T vlx, vly, vlz;
-                if (kAbsolute) {
-                    vlx = (T)vs[jl];
-                    vly = (T)vs[n + jl];
-                    vlz = (T)vs[2 * n + jl];
-                } else {
-                    const float4 t4 = vf[jl];
-                    vlx = (T)t4.x;
-                    vly = (T)t4.y;
-                    vlz = (T)t4.z;
-                }
+                const double4 ql = rel[jl];
+                const double vlx = vs[jl], vly = vs[n + jl], vlz = vs[2 * n + jl];
                 for (uint32_t j = j0; j < j1; ++j) {
                     const int src = (int)(j - b * 32);
-                    T dx = __shfl_sync(0xffffffffu, (T)ql.x, src) - xs;
-                    T dy = __shfl_sync(0xffffffffu, (T)ql.y, src) - ys;
-                    T dz = __shfl_sync(0xffffffffu, (T)ql.z, src) - zs;
-                    if (kAbsolute) {
-                        dx += ix;
-                        dy += iy;
-                        dz += iz;
-                    }
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    const bool in = valid && (all_in || r2 < rc2) && r2 > T(0);
-                    const T w0 = __shfl_sync(0xffffffffu, vlx, src) - vix;
-                    const T w1 = __shfl_sync(0xffffffffu, vly, src) - viy;
-                    const T w2 = __shfl_sync(0xffffffffu, vlz, src) - viz;
+                    const double dx = (__shfl_sync(0xffffffffu, ql.x, src) - xi.x) + ix;
+                    const double dy = (__shfl_sync(0xffffffffu, ql.y, src) - xi.y) + iy;
+                    const double dz = (__shfl_sync(0xffffffffu, ql.z, src) - xi.z) + iz;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    const bool in = valid && (all_in || r2 < rc2) && r2 > 0.0;
+                    const double w0 = __shfl_sync(0xffffffffu, vlx, src) - vix;
+                    const double w1 = __shfl_sync(0xffffffffu, vly, src) - viy;
+                    const double w2 = __shfl_sync(0xffffffffu, vlz, src) - viz;
                     if (!all_in && !__any_sync(0xffffffffu, in)) continue;
-                    T h, hr;
-                    pair_jac(r2, eps2, inv_rs, gp, h, hr);
-                    const T dw = dx * w0 + dy * w1 + dz * w2;
-                    const T c = in ? hr * dw : T(0);
-                    const T hh = in ? h : T(0);
+                    double h, hr;
+                    pair_jac(r2, eps2, inv_rs, h, hr);
+                    const double dw = dx * w0 + dy * w1 + dz * w2;
+                    const double c = in ? hr * dw : 0.0;
+                    const double hh = in ? h : 0.0;
                     ox += hh * w0 + c * dx;
                     oy += hh * w1 + c * dy;
                     oz += hh * w2 + c * dz;
                 }
             }
-            if (kAbsolute) {
-                o[0] += (double)ox;
-                o[1] += (double)oy;
-                o[2] += (double)oz;
-            } else {
-                two_sum_add(so[0], co[0], (float)ox);
-                two_sum_add(so[1], co[1], (float)oy);
-                two_sum_add(so[2], co[2], (float)oz);
-            }
+            o[0] += ox;
+            o[1] += oy;
+            o[2] += oz;
         }
-        if (!kAbsolute)
-            for (int d = 0; d < 3; ++d) o[d] = (double)so[d] + (double)co[d];
         if (valid) {
             out[i] += g.gm * o[0];
             out[n + i] += g.gm * o[1];
             out[2 * n + i] += g.gm * o[2];
         }
     }
+}
+
+// FP32 mode: the force kernel's traversal and arithmetic style (one-warp persistent CTAs,
+// bulk-copy tiles of the block-SoA coordinates and v, block culling, the all-inside fast path,
+// two j particles per lane in packed f32x2, FP32 TwoSum accumulation), for
+//   out_k += Gm sum_j [h(r) w + (h'(r)/r)(d.w) d],  w = v_j - v_k,
+//   h = g s^3, h'/r = -(r e / (2 sqrt(pi) r_s^3)) s^3 - 3 h s^2,  s = (r^2 + eps^2)^-1/2,
+//   e = exp(-r^2 / (4 r_s^2)),
+// g from the fitted polynomial (g'(x) = -x^2 exp(-x^2/4) / (2 sqrt(pi)) in closed form).  r^2
+// starts at kVjpTiny = 1e-20 like in the force kernel; r = 0 pairs are selected out (their w need
+// not vanish for coincident particles).
+constexpr float kVjpTiny = 1e-20f;
+constexpr int kVjpBlocksPerTile = 4;
+
+struct VjpConst2 {
+    f2 c[P3M_SPLIT_DEG + 1];
+    f2 c11, m1, one, eps2, tiny, ex2arg, c1, m3;
+};
+
+// h and h'/r of both halves of r2 (r2 includes kVjpTiny)
+__device__ __forceinline__ void pair_jac2(f2 r2, const VjpConst2 &k, f2 &h, f2 &hr)
+{
+    float r2l, r2h, s2l, s2h, al, ah;
+    const f2 s2 = f2_add(r2, k.eps2);
+    f2_unpack(r2, r2l, r2h);
+    f2_unpack(s2, s2l, s2h);
+    const f2 s = f2_pack(rsqrt_approx(s2l), rsqrt_approx(s2h));
+    const f2 r = f2_pack(sqrt_approx(r2l), sqrt_approx(r2h));
+    const f2 tau = f2_fma(r2, k.c11, k.m1);
+    f2 p = k.c[P3M_SPLIT_DEG];
+#pragma unroll
+    for (int q = P3M_SPLIT_DEG - 1; q >= 0; --q) p = f2_fma(p, tau, k.c[q]);
+    const f2 gval = f2_fma(f2_mul(r2, r), p, k.one);
+    const f2 ss = f2_mul(s, s);
+    const f2 s3 = f2_mul(ss, s);
+    h = f2_mul(gval, s3);
+    f2_unpack(f2_mul(r2, k.ex2arg), al, ah);  // -r^2 log2(e) / (4 r_s^2)
+    const f2 e = f2_pack(exp2f(al), exp2f(ah));
+    const f2 res3 = f2_mul(f2_mul(r, e), s3);
+    hr = f2_fma(res3, k.c1, f2_mul(f2_mul(h, ss), k.m3));  // c1 = -1/(2 sqrt(pi) r_s^3), m3 = -3
+}
+
+__global__ void __launch_bounds__(32, 32)
+    k_pairs_vjp_x2(const float *__restrict__ relx, const float *__restrict__ vfx,
+                   const float4 *__restrict__ rel, const double *__restrict__ pos,
+                   const float4 *__restrict__ block_box, const uint32_t *__restrict__ cell_start,
+                   const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
+                   const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPolyA gp, float rcull2,
+                   float rin2, uint32_t *__restrict__ cursor, uint32_t *__restrict__ flags,
+                   double *__restrict__ out)
+{
+    constexpr int kBlockFloats = 96;
+    __shared__ __align__(128) float sj[2][kVjpBlocksPerTile * kBlockFloats];
+    __shared__ __align__(128) float sv[2][kVjpBlocksPerTile * kBlockFloats];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ NeighbourF nbr[27];
+
+    const int lane = threadIdx.x;
+    const int64_t n = g.n;
+    const uint32_t n_work = *n_work_ptr;
+    const float rc2 = (float)(g.r_c * g.r_c);
+    const int nc = g.n_c;
+    VjpConst2 kc;
+#pragma unroll
+    for (int q = 0; q <= P3M_SPLIT_DEG; ++q) kc.c[q] = f2_pack(gp.c[q], gp.c[q]);
+    kc.c11 = f2_pack(gp.c[11], gp.c[11]);
+    kc.m1 = f2_pack(-1.0f, -1.0f);
+    kc.one = f2_pack(1.0f, 1.0f);
+    const float e2 = (float)(g.eps * g.eps);
+    kc.eps2 = f2_pack(e2, e2);
+    kc.tiny = f2_pack(kVjpTiny, kVjpTiny);
+    const float xa_ = (float)(-1.4426950408889634 / (4.0 * g.r_s * g.r_s));
+    kc.ex2arg = f2_pack(xa_, xa_);
+    const float c1 = (float)(-0.28209479177387814347 / (g.r_s * g.r_s * g.r_s));
+    kc.c1 = f2_pack(c1, c1);
+    kc.m3 = f2_pack(-3.0f, -3.0f);
+
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0u;
+    bool timed_out = false;
+
+    for (;;) {
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(cursor, 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= n_work) break;
+        const uint32_t item = order[slot];
+        const uint32_t cell = work[2 * (size_t)item];
+        const uint32_t first = work[2 * (size_t)item + 1];
+        const uint32_t cend = cell_start[cell + 1];
+        const int cx = (int)(cell % nc), cy = (int)((cell / nc) % nc), cz = (int)(cell / (nc * nc));
+        __syncwarp();  // the previous item is done with nbr
+        if (lane < 27) nbr[lane] = make_neighbour(g, cell_start, cx, cy, cz, lane);
+        __syncwarp();
+
+        const uint32_t i = first + lane;
+        const bool valid = i < cend;
+        const uint32_t ii = valid ? i : first;
+        const float4 xi = rel[ii];
+        const float xa = (float)pos[ii], ya = (float)pos[n + ii], za = (float)pos[2 * n + ii];
+        const float *vi = vfx + (ii >> 5) * kBlockFloats + (ii & 31);
+        const f2 vix2 = f2_pack(vi[0], vi[0]), viy2 = f2_pack(vi[32], vi[32]),
+                 viz2 = f2_pack(vi[64], vi[64]);
+        float sox = 0.0f, soy = 0.0f, soz = 0.0f, cox = 0.0f, coy = 0.0f, coz = 0.0f;
+
+        auto next_tile = [&](int &nb, uint32_t &b) {
+            while (nb < 27 && b * 32u >= nbr[nb].end) {
+                ++nb;
+                if (nb < 27) b = nbr[nb].start >> 5;
+            }
+        };
+        auto issue = [&](int nb, uint32_t b, int to) {
+            const uint32_t bend = min(b + kVjpBlocksPerTile, (nbr[nb].end + 31) >> 5);
+            const uint32_t bytes = (bend - b) * (uint32_t)(kBlockFloats * sizeof(float));
+            mbar_expect_tx(&bar[to], 2 * bytes);
+            bulk_load(&sj[to][0], relx + (size_t)b * kBlockFloats, bytes, &bar[to]);
+            bulk_load(&sv[to][0], vfx + (size_t)b * kBlockFloats, bytes, &bar[to]);
+        };
+
+        int nb_c = 0;
+        uint32_t b_c = nbr[0].start >> 5;
+        next_tile(nb_c, b_c);
+        int buf = 0;
+        if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
+        while (nb_c < 27) {
+            const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
+            const uint32_t bend = min(b_c + kVjpBlocksPerTile, (nend + 31) >> 5);
+            int nb_n = nb_c;
+            uint32_t b_n = bend;
+            next_tile(nb_n, b_n);
+            __syncwarp();  // every lane is done with the other buffer before it is refilled
+            if (nb_n < 27 && lane == 0) issue(nb_n, b_n, buf ^ 1);
+            const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u);
+            parity ^= 1u << buf;
+            if (__any_sync(0xffffffffu, !ok)) {
+                timed_out = true;
+                if (nb_n < 27) mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
+                break;
+            }
+            const NeighbourF &q = nbr[nb_c];
+            const float xs = (xi.x - q.sx) - q.rx;
+            const float ys = (xi.y - q.sy) - q.ry;
+            const float zs = (xi.z - q.sz) - q.rz;
+            const f2 xs2 = f2_pack(xs, xs), ys2 = f2_pack(ys, ys), zs2 = f2_pack(zs, zs);
+            const float cxs = xa - q.imx, cys = ya - q.imy, czs = za - q.imz;
+            f2 ox = 0, oy = 0, oz = 0;
+
+            // pair (p, p+1) of the block; lo/hi: which halves take part; test: r < r_c
+            auto pair_vjp = [&](const float *bx, const float *bv, uint32_t p, bool lo, bool hi,
+                                bool test) {
+                const f2 dx = f2_sub(*(const f2 *)(bx + p), xs2);
+                const f2 dy = f2_sub(*(const f2 *)(bx + 32 + p), ys2);
+                const f2 dz = f2_sub(*(const f2 *)(bx + 64 + p), zs2);
+                const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, kc.tiny)));
+                float r2l, r2h;
+                f2_unpack(r2, r2l, r2h);
+                const bool inl = lo && r2l > kVjpTiny && (!test || r2l < rc2);
+                const bool inh = hi && r2h > kVjpTiny && (!test || r2h < rc2);
+                if (test && !__any_sync(0xffffffffu, inl || inh)) return;
+                f2 h, hr;
+                pair_jac2(r2, kc, h, hr);
+                const f2 wx = f2_sub(*(const f2 *)(bv + p), vix2);
+                const f2 wy = f2_sub(*(const f2 *)(bv + 32 + p), viy2);
+                const f2 wz = f2_sub(*(const f2 *)(bv + 64 + p), viz2);
+                const f2 dw = f2_fma(dz, wz, f2_fma(dy, wy, f2_mul(dx, wx)));
+                float hl, hh, cl, ch;
+                f2_unpack(h, hl, hh);
+                f2_unpack(f2_mul(hr, dw), cl, ch);
+                const f2 hs = f2_pack(inl ? hl : 0.0f, inh ? hh : 0.0f);
+                const f2 cs = f2_pack(inl ? cl : 0.0f, inh ? ch : 0.0f);
+                ox = f2_fma(cs, dx, f2_fma(hs, wx, ox));
+                oy = f2_fma(cs, dy, f2_fma(hs, wy, oy));
+                oz = f2_fma(cs, dz, f2_fma(hs, wz, oz));
+            };
+
+            for (uint32_t b = b_c; b < bend; ++b) {
+                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
+                const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
+                const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
+                if (!__any_sync(0xffffffffu, valid && ex * ex + ey * ey + ez * ez < rcull2)) continue;
+                const uint32_t j0 = max(b * 32, nstart) - b * 32;
+                const uint32_t j1 = min(b * 32 + 32, nend) - b * 32;
+                const float *bx = sj[buf] + (b - b_c) * kBlockFloats;
+                const float *bv = sv[buf] + (b - b_c) * kBlockFloats;
+                const float fx = fmaxf(cxs - lo.x, hi.x - cxs);
+                const float fy = fmaxf(cys - lo.y, hi.y - cys);
+                const float fz = fmaxf(czs - lo.z, hi.z - czs);
+                const bool test =
+                    !__all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2);
+                uint32_t p = j0 & ~1u;
+                if ((j0 & 1u) && j0 < j1) {
+                    pair_vjp(bx, bv, p, false, true, true);
+                    p += 2;
+                }
+                if (test) {
+                    for (; p + 1 < j1; p += 2) pair_vjp(bx, bv, p, true, true, true);
+                } else {
+#pragma unroll 2
+                    for (; p + 1 < j1; p += 2) pair_vjp(bx, bv, p, true, true, false);
+                }
+                if (p < j1) pair_vjp(bx, bv, p, true, false, true);
+            }
+            float lo_, hi_;
+            f2_unpack(ox, lo_, hi_);
+            two_sum_add(sox, cox, lo_ + hi_);
+            f2_unpack(oy, lo_, hi_);
+            two_sum_add(soy, coy, lo_ + hi_);
+            f2_unpack(oz, lo_, hi_);
+            two_sum_add(soz, coz, lo_ + hi_);
+            buf ^= 1;
+            nb_c = nb_n;
+            b_c = b_n;
+        }
+        if (timed_out) break;
+        if (valid) {
+            out[i] += g.gm * ((double)sox + (double)cox);
+            out[n + i] += g.gm * ((double)soy + (double)coy);
+            out[2 * n + i] += g.gm * ((double)soz + (double)coz);
+        }
+    }
+    if (timed_out && lane == 0) atomicOr(flags, P3M_FLAG_TIMEOUT);
 }
 
 // ------------------------------------------------------------------ potential energy
@@ -682,24 +831,33 @@ cudaError_t vjp_mesh(p3m_ctx *c, const double *v_slots, double *out_slots)
     return cudaGetLastError();
 }
 
-template <typename T>
 cudaError_t vjp_pairs(p3m_ctx *c, const double *v_slots, double *out_slots)
 {
-    GPolyA gp;
-    for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_vjp<T>, 32, 0);
+    const bool fp32 = c->precision == P3M_PREC_MIXED;
+    cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_vjp_x2, 32, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_vjp64, 32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     e = cudaMemsetAsync(c->counters + 3, 0, sizeof(uint32_t), c->stream);
     if (e != cudaSuccess) return e;
     const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
     const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
+    const float rcull2 = (float)(rcull * rcull), rin2 = rin > 0.0 ? (float)(rin * rin) : 0.0f;
     c->launches += 1;
-    k_pairs_vjp<T><<<c->num_sms * per_sm, 32, 0, c->stream>>>(
-        (const typename V4Of<T>::type *)c->rel, c->pos, c->block_box, c->adj_vf, v_slots,
-        c->cell_start, c->work, c->work_order, c->work_off + c->g.n_cells, c->g, gp,
-        (float)(rcull * rcull), rin > 0.0 ? (float)(rin * rin) : 0.0f, c->counters + 3, out_slots);
+    if (fp32) {
+        GPolyA gp;
+        for (int k = 0; k < 12; ++k) gp.c[k] = c->gpoly[k];
+        k_pairs_vjp_x2<<<c->num_sms * per_sm, 32, 0, c->stream>>>(
+            c->relx, c->adj_vfx, (const float4 *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
+            c->work_order, c->work_off + c->g.n_cells, c->g, gp, rcull2, rin2, c->counters + 3,
+            c->counters + 1, out_slots);
+    } else {
+        k_pairs_vjp64<<<c->num_sms * per_sm, 32, 0, c->stream>>>(
+            (const double4 *)c->rel, c->pos, c->block_box, v_slots, c->cell_start, c->work,
+            c->work_order, c->work_off + c->g.n_cells, c->g, rcull2, rin2, c->counters + 3,
+            out_slots);
+    }
     return cudaGetLastError();
 }
 
@@ -708,7 +866,8 @@ cudaError_t vjp_pairs(p3m_ctx *c, const double *v_slots, double *out_slots)
 cudaError_t launch_to_slots(p3m_ctx *c, const double *v, double *vs)
 {
     c->launches += 1;
-    k_to_slots<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(v, c->pid, c->g.n, vs, c->adj_vf);
+    k_to_slots<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(
+        v, c->pid, c->g.n, vs, c->precision == P3M_PREC_MIXED ? c->adj_vfx : nullptr);
     return cudaGetLastError();
 }
 
@@ -718,10 +877,10 @@ cudaError_t launch_force_vjp(p3m_ctx *c, const double *v_slots, double *out_slot
     if (e != cudaSuccess) return e;
     if (c->precision == P3M_PREC_MIXED) {
         e = vjp_mesh<float, cufftComplex>(c, v_slots, out_slots);
-        if (e == cudaSuccess && c->short_range) e = vjp_pairs<float>(c, v_slots, out_slots);
+        if (e == cudaSuccess && c->short_range) e = vjp_pairs(c, v_slots, out_slots);
     } else {
         e = vjp_mesh<double, cufftDoubleComplex>(c, v_slots, out_slots);
-        if (e == cudaSuccess && c->short_range) e = vjp_pairs<double>(c, v_slots, out_slots);
+        if (e == cudaSuccess && c->short_range) e = vjp_pairs(c, v_slots, out_slots);
     }
     return e;
 }

@@ -189,7 +189,7 @@ void release(p3m_ctx *c)
                     c->work_order, c->work_order_alt, c->block_box, c->tab_invw2,
                     c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac,
                     c->tab_origin,
-                    c->adj_u,     c->adj_vf,   c->adj_vs,       c->adj_out,  c->kself,
+                    c->adj_u,     c->adj_vfx,  c->adj_vs,       c->adj_out,  c->kself,
                     c->li,        c->relx};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -543,7 +543,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->fac_table, 8 * 4 * (size_t)P3M_MAX_GRAPH_STEPS},
             {(void **)&c->step_idx, 16},      {(void **)&c->cur_fac, 32},
             {(void **)&c->kself, 8 * 27},     {(void **)&c->li, 8 * 4},
-            {(void **)&c->adj_u, 3 * real * M3}, {(void **)&c->adj_vf, 16 * N},
+            {(void **)&c->adj_u, 3 * real * M3}, {(void **)&c->adj_vfx, opt.precision == P3M_PREC_MIXED ? 384 * ((N + 31) / 32) : 16},
             {(void **)&c->adj_vs, 24 * N},    {(void **)&c->adj_out, 24 * N},
         };
         for (auto &a : allocs) {
@@ -557,6 +557,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         if (rc != P3M_OK) break;
         cudaMemsetAsync(c->counters, 0, 16, c->stream);
         cudaMemsetAsync(c->pair_count, 0, 64, c->stream);
+        if (opt.precision == P3M_PREC_MIXED)  // padding past the last particle stays zero
+            cudaMemsetAsync(c->adj_vfx, 0, 384 * ((N + 31) / 32), c->stream);
 
         // per-axis tables (FP64 on the host, stored in the mesh precision)
         const double h = box / mesh, rs2 = c->short_range ? g.r_s * g.r_s : 0.0;

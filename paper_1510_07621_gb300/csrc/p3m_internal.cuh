@@ -94,7 +94,8 @@ struct p3m_ctx {
 
     // reverse-mode derivative buffers
     void *adj_u;       // three real meshes (vector deposit; also target-mesh staging)
-    float4 *adj_vf;    // v in slot order, FP32
+    float *adj_vfx;    // FP32 mode: v in slot order as block-SoA (per 32 slots vx[32] vy[32] vz[32];
+                       // zero past the last particle)
     double *adj_vs;    // v in slot order, FP64 [3][n]
     double *adj_out;   // result in slot order [3][n]
 
@@ -277,7 +278,7 @@ cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst);
 cudaError_t launch_diag(p3m_ctx *c, double *host_out /* [4]: px py pz 2*kinetic*m*a^2 */);
 
 // ------------------------------------------------------------------ launchers (adjoint.cu)
-// vs (and adj_vf) = v permuted from caller order into slot order
+// vs (and, FP32 mode, adj_vfx) = v permuted from caller order into slot order
 cudaError_t launch_to_slots(p3m_ctx *c, const double *v, double *vs);
 // out_slots = (dA/dx)^T v_slots at the current (sorted, evaluated) state
 cudaError_t launch_force_vjp(p3m_ctx *c, const double *v_slots, double *out_slots);
