@@ -464,12 +464,14 @@ __global__ void __launch_bounds__(32, 32)
                     in[u][0] = l < rc2;
                     in[u][1] = h < rc2;
                     any[u] = __any_sync(0xffffffffu, in[u][0] || in[u][1]);
-                    cnt += (in[u][0] && l > kTiny) + (in[u][1] && h > kTiny);
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    if (!any[u]) continue;
+                    if (!any[u]) continue;  // (then no lane counts a pair either)
                     ++n_eval;
+                    float l, h;
+                    f2_unpack(r2[u], l, h);
+                    cnt += (in[u][0] && l > kTiny) + (in[u][1] && h > kTiny);
                     float fl, fh;
                     f2_unpack(pair_factor2(r2[u], kc), fl, fh);
                     const f2 f = f2_pack(in[u][0] ? fl : 0.0f, in[u][1] ? fh : 0.0f);
