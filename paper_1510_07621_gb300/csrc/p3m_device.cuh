@@ -73,6 +73,13 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return y;
 }
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float y;

@@ -287,14 +287,17 @@ __device__ __forceinline__ f2 pair_factor2(f2 r2, const PairConst2 &k)
     const f2 s2 = f2_add(r2, k.eps2);
     f2_unpack(r2, r2l, r2h);
     f2_unpack(s2, s2l, s2h);
-    const f2 s = f2_pack(rsqrt_approx(s2l), rsqrt_approx(s2h));
+    // s^3 = (r^2 + eps^2)^-3/2 as rsqrt * rcp: one FP32 multiply instead of two (the MUFU
+    // pipe has room to spare)
+    const f2 s3 = f2_mul(f2_pack(rsqrt_approx(s2l), rsqrt_approx(s2h)),
+                         f2_pack(rcp_approx(s2l), rcp_approx(s2h)));
     const f2 r3 = f2_mul(r2, f2_pack(sqrt_approx(r2l), sqrt_approx(r2h)));
     const f2 tau = f2_fma(r2, k.c11, k.m1);
     f2 p = k.c[P3M_SPLIT_DEG];
 #pragma unroll
     for (int q = P3M_SPLIT_DEG - 1; q >= 0; --q) p = f2_fma(p, tau, k.c[q]);
     const f2 gval = f2_fma(r3, p, k.one);
-    return f2_mul(gval, f2_mul(f2_mul(s, s), s));
+    return f2_mul(gval, s3);
 }
 
 template <bool kBatched>
