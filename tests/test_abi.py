@@ -71,6 +71,10 @@ def test_init_argument_checks(lib, args, needle):
 
 
 def test_null_context_is_rejected(lib):
+    assert lib.p3m_ensemble_set_batched(None, 1) == _lib.P3M_EINVAL
+    assert lib.p3m_energy(None, None, None) == _lib.P3M_EINVAL
+    assert lib.p3m_track_energy(None, 1) == _lib.P3M_EINVAL
+    assert lib.p3m_measure_fma_peak(0, None) == _lib.P3M_EINVAL
     assert lib.p3m_step(None, 0.1, 0.01) == _lib.P3M_EINVAL
     assert lib.p3m_forces(None, 0.1, None, 0) == _lib.P3M_EINVAL
     assert lib.p3m_get_geometry(None, None, None, None, None) == _lib.P3M_EINVAL

@@ -78,7 +78,7 @@ def _adversarial(box=64.0, mesh=32):
     return np.concatenate([one_cell, edge], axis=1), dict(box=box, mesh=mesh)
 
 
-@pytest.mark.parametrize("sub_bits", [0, 2])
+@pytest.mark.parametrize("sub_bits", [0, 2, 5])
 @pytest.mark.parametrize("case", ["eds32", "clustered48", "adversarial"])
 def test_keys_order_and_cell_ranges_bit_exact(P3M, case, sub_bits):
     if case == "adversarial":
@@ -304,3 +304,12 @@ def test_lcdm_steps_match_oracle(P3M):
     dx -= kw["box"] * np.round(dx / kw["box"])
     assert np.max(np.abs(dx)) <= 1e-11 * kw["box"]
     assert np.max(np.abs(gmom - m)) <= 1e-9 * np.max(np.abs(m))
+
+
+def test_fma_probe_reports_plausible_rates(P3M):
+    """The FMA throughput probe: positive, FP32 far above FP64, FP32 below 2x the nominal peak
+    (152 SMs x 128 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s)."""
+    from paper_1510_07621_gb300 import measure_fma_peak
+    f32, f64 = measure_fma_peak(False), measure_fma_peak(True)
+    assert 1.0 < f32 < 161.0
+    assert 0.01 < f64 < f32
