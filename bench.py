@@ -150,6 +150,36 @@ def oracle_step_time(pos, mom, n_sample, seed):
     return total, O.oracle_threads(), desc
 
 
+def oracle_pair_time_one_core(x, n_sample, seed):
+    """Seconds one host core needs for the oracle's pair sum of n_sample sampled particles of
+    the wrapped positions x (a child process with OMP_NUM_THREADS=1).  Returns (seconds,
+    particles sampled) or (None, 0) if the child failed."""
+    import subprocess
+    import tempfile
+    w = WORKLOAD
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "x.npy")
+        np.save(path, x)
+        code = (
+            "import sys, time, numpy as np\n"
+            f"sys.path.insert(0, {ROOT!r})\n"
+            "import p3m_synth as S\n"
+            "from oracle import p3m_oracle as O\n"
+            f"x = np.load({path!r}); n = x.shape[1]\n"
+            f"p = O.Params({w['box']!r}, n, {w['mesh']!r}, {w['r_s_cells']!r}, {w['cutoff']!r}, "
+            f"{w['softening']!r})\n"
+            f"tg = np.unique((S.uniform01({seed}, {n_sample}) * n).astype(np.int64) % n)\n"
+            "t0 = time.perf_counter(); O.sr_accel(x, p, targets=tg)\n"
+            "print(time.perf_counter() - t0, tg.size, O.oracle_threads())\n")
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=600)
+        if r.returncode != 0:
+            return None, 0
+        sec, size, threads = r.stdout.split()[-3:]
+        return (float(sec), int(size)) if int(threads) == 1 else (None, 0)
+
+
 # ---------------------------------------------------------------- replicas across ranks
 
 
@@ -369,7 +399,24 @@ def run_ours(args, rank, world, local_rank, dist):
             sim.get_particles(hp, hm)
             snap_pos, snap_mom = hp, hm
         sec, threads, desc = oracle_step_time(snap_pos, snap_mom, args.cpu_sample, 99)
+        # the same step with the pair sum on one core (mesh part and kick/drift as measured)
+        from oracle import p3m_oracle as O
+        xw = O.wrap(snap_pos, w["box"])
+        sec1, size1 = oracle_pair_time_one_core(xw, max(1000, args.cpu_sample // 4), 98)
+        one_core = None
+        if sec1:
+            t0 = time.perf_counter()
+            O.sr_accel(xw, O.Params(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"],
+                                    w["softening"]),
+                       targets=np.unique((S.uniform01(98, max(1000, args.cpu_sample // 4)) * n)
+                                         .astype(np.int64) % n))
+            sec_many = time.perf_counter() - t0
+            sec_one = sec + (sec1 - sec_many) * n / size1
+            one_core = {"value": n / sec_one, "unit": UNIT, "cores": 1,
+                        "sample": f"pair sum of {size1} sampled particles on one core, scaled; "
+                                  "mesh force and kick/drift as in the multi-core figure"}
         out["cpu_baseline"] = {"value": n / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "one_core": one_core,
                                "sample": desc + "; on the GPU run's a~1 snapshot",
                                "seconds_per_step_estimate": sec}
     sim.close()
