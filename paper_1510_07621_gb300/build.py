@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libp3m.so")
-SOURCES = ["api.cu", "sort.cu", "mesh.cu", "pair.cu", "integrate.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "ensemble.cu", "derivatives.cu", "sort.cu", "mesh.cu", "pair.cu",
+           "integrate.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
