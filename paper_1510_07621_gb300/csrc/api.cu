@@ -78,25 +78,36 @@ double quad(const p3m_cosmology &cs, double a1, double a2, int power)
 }
 
 // ---------------------------------------------------------------- split factor fit
-// g(x) = erfc(x/2) + x/sqrt(pi) exp(-x^2/4) = 1 + x^3 Q(x^2).  Q is smooth in u = x^2; it is
-// interpolated at 40 Chebyshev-Gauss nodes of u in [0, u_c], u_c = (r_c/r_s)^2, truncated to
-// degree P3M_SPLIT_DEG (a near-minimax polynomial), and rewritten in monomial form in tau = 2u/u_c - 1
-// for Horner evaluation in FP32.  The kernel evaluates g = 1 + r^3 Q'(tau) directly from
-// r^2, so the coefficients are scaled by r_s^-3 and tau = r^2 (2 / (u_c r_s^2)) - 1.
+// g(x) = erfc(x/2) + x/sqrt(pi) exp(-x^2/4) = 1 + x^3 Q(x^2).  Q is smooth (entire) in u = x^2;
+// it is interpolated at Chebyshev-Gauss nodes of u in [0, u_c], u_c = (r_c/r_s)^2, truncated to
+// the wanted degree (a near-minimax polynomial), and rewritten in monomial form in
+// tau = 2u/u_c - 1 for Horner evaluation (the monomial coefficients stay below 0.03 in size up to
+// degree 22, so the rewriting costs no accuracy).  The kernels evaluate g = 1 + r^3 Q'(tau)
+// directly from r^2, so the coefficients are scaled by r_s^-3 and tau = r^2 (2 / (u_c r_s^2)) - 1.
 
+// Q(u): below u = 1 from its Taylor series (the closed form cancels there),
+// Q(u) = (1/sqrt(pi)) sum_{n>=1} (-1)^n u^(n-1) 2n / (4^n n! (2n+1)); above, (g - 1)/(u x).
 double split_q(double u)
 {
-    const double x = sqrt(u), inv_sqrt_pi = 0.56418958354775628695;
-    if (u < 1e-6) return -inv_sqrt_pi / 6.0 * (1.0 - 0.15 * u);  // series: -(1/(6 sqrt pi))(1 - 3u/20)
+    const double inv_sqrt_pi = 0.56418958354775628695;
+    if (u < 1.0) {
+        double b = -0.25, sum = 0.0;  // b_n = (-1)^n u^(n-1) / (4^n n!), from b_1 = -1/4
+        for (int n = 1; n <= 30; ++n) {
+            sum += b * (2.0 * n) / (2.0 * n + 1.0);
+            b *= -0.25 * u / (n + 1);
+        }
+        return inv_sqrt_pi * sum;
+    }
+    const double x = sqrt(u);
     const double gval = erfc(0.5 * x) + x * inv_sqrt_pi * exp(-0.25 * u);
     return (gval - 1.0) / (u * x);
 }
 
-void fit_split_poly(double cutoff_in_rs, double r_s, float out[12])
+// Monomial coefficients mono[0..deg] of Q in tau (unscaled), from `nodes` Chebyshev nodes.
+void fit_split_mono(double cutoff_in_rs, int deg, int nodes, double *mono)
 {
-    const int deg = P3M_SPLIT_DEG, nodes = 40;
     const double uc = cutoff_in_rs * cutoff_in_rs;
-    double cheb[deg + 1] = {0};
+    std::vector<double> cheb(deg + 1, 0.0), tk_prev(deg + 1, 0.0), tk(deg + 1, 0.0), next(deg + 1);
     for (int j = 0; j < nodes; ++j) {
         const double th = M_PI * (j + 0.5) / nodes, t = cos(th);
         const double q = split_q(0.5 * (t + 1.0) * uc);
@@ -104,26 +115,43 @@ void fit_split_poly(double cutoff_in_rs, double r_s, float out[12])
     }
     for (int k = 0; k <= deg; ++k) cheb[k] *= (k == 0 ? 1.0 : 2.0) / nodes;
     // Chebyshev series -> monomials: T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1}
-    double tk_prev[deg + 1] = {0}, tk[deg + 1] = {0}, mono[deg + 1] = {0};
+    for (int i = 0; i <= deg; ++i) mono[i] = 0.0;
     tk_prev[0] = 1.0;
-    tk[1] = 1.0;
     mono[0] += cheb[0];
-    for (int i = 0; i <= deg; ++i) mono[i] += cheb[1] * tk[i];
+    if (deg >= 1) {
+        tk[1] = 1.0;
+        for (int i = 0; i <= deg; ++i) mono[i] += cheb[1] * tk[i];
+    }
     for (int k = 2; k <= deg; ++k) {
-        double next[deg + 1] = {0};
-        for (int i = 0; i <= deg; ++i) {
-            next[i] = -tk_prev[i] + (i > 0 ? 2.0 * tk[i - 1] : 0.0);
-        }
+        for (int i = 0; i <= deg; ++i) next[i] = -tk_prev[i] + (i > 0 ? 2.0 * tk[i - 1] : 0.0);
         for (int i = 0; i <= deg; ++i) {
             mono[i] += cheb[k] * next[i];
             tk_prev[i] = tk[i];
             tk[i] = next[i];
         }
     }
-    const double inv_rs3 = 1.0 / (r_s * r_s * r_s);
-    for (int i = 0; i <= deg; ++i) out[i] = (float)(mono[i] * inv_rs3);
-    for (int i = deg + 1; i < 11; ++i) out[i] = 0.0f;
+}
+
+// FP32 coefficients (degree P3M_SPLIT_DEG) into out[0..10], tau's scale into out[11].
+void fit_split_poly(double cutoff_in_rs, double r_s, float out[12])
+{
+    double mono[P3M_SPLIT_DEG + 1];
+    fit_split_mono(cutoff_in_rs, P3M_SPLIT_DEG, 40, mono);
+    const double uc = cutoff_in_rs * cutoff_in_rs, inv_rs3 = 1.0 / (r_s * r_s * r_s);
+    for (int i = 0; i <= P3M_SPLIT_DEG; ++i) out[i] = (float)(mono[i] * inv_rs3);
+    for (int i = P3M_SPLIT_DEG + 1; i < 11; ++i) out[i] = 0.0f;
     out[11] = (float)(2.0 / (uc * r_s * r_s));
+}
+
+// FP64 coefficients (degree P3M_SPLIT_DEG64, largest error in g about 4e-14 relative) into
+// out[0..P3M_SPLIT_DEG64], tau's scale into out[P3M_SPLIT_DEG64 + 1].
+void fit_split_poly64(double cutoff_in_rs, double r_s, double *out)
+{
+    double mono[P3M_SPLIT_DEG64 + 1];
+    fit_split_mono(cutoff_in_rs, P3M_SPLIT_DEG64, 64, mono);
+    const double uc = cutoff_in_rs * cutoff_in_rs, inv_rs3 = 1.0 / (r_s * r_s * r_s);
+    for (int i = 0; i <= P3M_SPLIT_DEG64; ++i) out[i] = mono[i] * inv_rs3;
+    out[P3M_SPLIT_DEG64 + 1] = 2.0 / (uc * r_s * r_s);
 }
 
 // ---------------------------------------------------------------- phase timing
@@ -538,6 +566,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         }
         c->green_const = -4.0 * M_PI * (g.gm / (h * h * h)) / ((double)M3);
         fit_split_poly(cutoff_in_rs, g.r_s, c->gpoly);
+        fit_split_poly64(cutoff_in_rs, g.r_s, c->gpoly64);
         if (c->precision == P3M_PREC_MIXED) {
             std::vector<float> f(M);
             const std::vector<double> *src[3] = {&tk, &tkg, &tg};

@@ -7,6 +7,16 @@
 
 #include "p3m.h"
 
+// Degree of the fitted FP32 split factor Q (Chebyshev fit on [0, r_c]).  Its largest error in g
+// is 5.8e-6 (near r_c, where g = 0.0175).  Against the FP64 oracle the FP32 short-range force
+// then differs by 7.50e-6 relative RMS on the 32^3 Zel'dovich state at a = 0.02 (7.31e-6 at
+// degree 10, 1.8e-5 at degree 7: the FP32 rounding of nearly cancelling pair sums dominates)
+// and by 1.7e-6 on a clustered state.
+#define P3M_SPLIT_DEG 8
+// Degree of the FP64 split factor of the FP64 pair kernel: its largest error in g is about
+// 4e-14 relative (at r_c), far below the FP64 mode's 1e-12 parity bar.
+#define P3M_SPLIT_DEG64 18
+
 // Chaining-cell geometry, mesh constants and the per-evaluation scalars every kernel needs.
 struct P3MGeom {
     double box;       // L
@@ -72,6 +82,8 @@ struct p3m_ctx {
     double green_const;
     float gpoly[12];  // FP32 split factor: g = 1 + r^3 Q(tau), Q = sum gpoly[k] tau^k
                       // (k <= P3M_SPLIT_DEG), tau = r^2 gpoly[11] - 1
+    double gpoly64[P3M_SPLIT_DEG64 + 2];  // the same in FP64 (degree P3M_SPLIT_DEG64); the
+                                          // last entry is tau's scale
     cufftHandle plan_r2c, plan_c2r, plan_c2r_one;  // R2C, batched 3 x C2R, single C2R
     bool plans_made;
 
@@ -128,12 +140,6 @@ enum {
 
 #define P3M_MAX_GRAPH_STEPS 4096  // steps per p3m_run_steps / p3m_ensemble_run call
 #define P3M_SORT_TILE 4096   // keys per radix-sort tile (256 threads x 16)
-// Degree of the fitted FP32 split factor Q (Chebyshev fit on [0, r_c]).  Its largest error in g
-// is 5.8e-6 (near r_c, where g = 0.0175).  Against the FP64 oracle the FP32 short-range force
-// then differs by 7.50e-6 relative RMS on the 32^3 Zel'dovich state at a = 0.02 (7.31e-6 at
-// degree 10, 1.8e-5 at degree 7: the FP32 rounding of nearly cancelling pair sums dominates)
-// and by 1.7e-6 on a clustered state.
-#define P3M_SPLIT_DEG 8
 #define P3M_PAIR_TI 32       // i-particles per pair work item (one per lane of a warp)
 #define P3M_PAIR_TJ 128      // j-particles per shared-memory tile (4 blocks of 32)
 #define P3M_FLAG_TIMEOUT 1u  // counters[1] bit: a bounded wait gave up

@@ -37,13 +37,26 @@ constexpr int kTJ = P3M_PAIR_TJ;  // 128
 constexpr int kBlocksPerTile = kTJ / 32;
 constexpr int kBlocksPerTileX2 = 4;  // FP32 kernel: 128 j particles (1.5 KB) per tile
 
-// g(r/r_s) (r^2 + eps^2)^-3/2 for one pair in FP64, g from erfc and exp.
-__device__ __forceinline__ double pair_factor64(double r2, double eps2, double inv_rs)
+// Coefficients of the FP64 split factor (the context's gpoly64): g = 1 + r^3 sum_k c[k] tau^k
+// (k <= P3M_SPLIT_DEG64), tau = r^2 c[P3M_SPLIT_DEG64 + 1] - 1.
+struct GPoly64 {
+    double c[P3M_SPLIT_DEG64 + 2];
+};
+
+// g(r/r_s) (r^2 + eps^2)^-3/2 for one pair in FP64, g from the FP64 fit (largest error about
+// 4e-14 relative): rsqrt and a Horner chain instead of sqrt, a division, erfc and exp, which
+// all run on GB300's narrow FP64 pipe.  For r2 = 0 the result is not finite; callers select
+// such pairs out.
+__device__ __forceinline__ double pair_factor64(double r2, double eps2, const GPoly64 &gp)
 {
-    const double s = 1.0 / sqrt(r2 + eps2);
-    const double x = sqrt(r2) * inv_rs;
-    const double g = erfc(0.5 * x) + x * 0.56418958354775628695 * exp(-0.25 * x * x);
-    return g * s * s * s;
+    const double s = rsqrt(r2 + eps2);
+    const double r3 = r2 * (r2 * rsqrt(r2));
+    const double tau = fma(r2, gp.c[P3M_SPLIT_DEG64 + 1], -1.0);
+    double p = gp.c[P3M_SPLIT_DEG64];
+#pragma unroll
+    for (int k = P3M_SPLIT_DEG64 - 1; k >= 0; --k) p = fma(p, tau, gp.c[k]);
+    const double gval = fma(r3, p, 1.0);
+    return gval * (s * s * s);
 }
 
 struct Neighbour {
@@ -55,7 +68,7 @@ __global__ void __launch_bounds__(32)
     k_pairs64(const double4 *__restrict__ rel, const double *__restrict__ pos,
             const float4 *__restrict__ block_box, const uint32_t *__restrict__ cell_start,
             const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
-            const uint32_t *__restrict__ n_work_ptr, P3MGeom g, float rcull2, float rin2,
+            const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPoly64 gp, float rcull2, float rin2,
             const double *__restrict__ acc_in, double *__restrict__ acc_out,
             double *__restrict__ mom, double kfac, const double *__restrict__ kfac_dev,
             uint32_t *__restrict__ counters, unsigned long long *__restrict__ pair_count)
@@ -70,7 +83,6 @@ __global__ void __launch_bounds__(32)
     const uint32_t n_work = *n_work_ptr;
     const double rc2 = g.r_c * g.r_c;
     const double eps2 = g.eps * g.eps;
-    const double inv_rs = 1.0 / g.r_s;
     const int nc = g.n_c;
 
     if (lane == 0) {
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(32)
                         const double dx = (qj.x - xs) + ix, dy = (qj.y - ys) + iy, dz = (qj.z - zs) + iz;
                         const double r2 = dx * dx + dy * dy + dz * dz;
                         const bool in = valid && r2 > 0.0;
-                        double f = pair_factor64(r2, eps2, inv_rs);
+                        double f = pair_factor64(r2, eps2, gp);
                         f = in ? f : 0.0;
                         px += f * dx;
                         py += f * dy;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(32)
                     const bool in = valid && r2 < rc2 && r2 > 0.0;
                     if (!__any_sync(0xffffffffu, in)) continue;
                     ++n_eval;
-                    double f = pair_factor64(r2, eps2, inv_rs);
+                    double f = pair_factor64(r2, eps2, gp);
                     f = in ? f : 0.0;
                     px += f * dx;
                     py += f * dy;
@@ -598,6 +610,8 @@ cudaError_t pairs64_impl(p3m_ctx *c, const double *acc_in, double *acc_out, doub
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const int grid = c->num_sms * per_sm;
+    GPoly64 gp;
+    for (int k = 0; k < P3M_SPLIT_DEG64 + 2; ++k) gp.c[k] = c->gpoly64[k];
     // culling radii: r_c widened (narrowed) by more than the FP32 rounding of absolute
     // coordinates up to the box size
     const double rcull = c->g.r_c * (1.0 + 1e-4) + c->g.box * 1e-6;
@@ -605,7 +619,7 @@ cudaError_t pairs64_impl(p3m_ctx *c, const double *acc_in, double *acc_out, doub
     c->launches += 1;
     k_pairs64<<<grid, 32, 0, c->stream>>>(
         (const double4 *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
-        c->work_order, c->work_off + c->g.n_cells, c->g, (float)(rcull * rcull),
+        c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
         rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, kfac_dev,
         c->counters, c->pair_count);
     return cudaGetLastError();
