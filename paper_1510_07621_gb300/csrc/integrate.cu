@@ -27,7 +27,10 @@ __device__ __forceinline__ double wrap_box(double x, double L)
     // x = fmod(x, L); x < 0 -> x += L; x >= L -> x -= L.  Inside [0, L) (the common case after
     // a drift) every step leaves x unchanged, and fmod(x, L) == x for -L < x < L: the FP64
     // sequence, slow on GB300's FP64 pipe, runs only for the rest.
-    if (x >= 0.0 && x < L) return x;
+    // x in [0, L) as integer compares of the bit patterns (IEEE order of non-negative doubles;
+    // -0.0 and NaN take the full sequence, which leaves -0.0 unchanged, as this test would)
+    const long long xb = __double_as_longlong(x);
+    if (xb >= 0 && xb < __double_as_longlong(L)) return x;
     if (!(x > -L && x < L)) x = fmod(x, L);
     if (x < 0.0) x = __dadd_rn(x, L);
     if (x >= L) x = __dadd_rn(x, -L);

@@ -28,7 +28,10 @@ __device__ __forceinline__ double wrap_box(double x, double L)
     // x = fmod(x, L); x < 0 -> x += L; x >= L -> x -= L.  Inside [0, L) (the common case after
     // a drift) every step leaves x unchanged, and fmod(x, L) == x for -L < x < L: the FP64
     // sequence, slow on GB300's FP64 pipe, runs only for the rest.
-    if (x >= 0.0 && x < L) return x;
+    // x in [0, L) as integer compares of the bit patterns (IEEE order of non-negative doubles;
+    // -0.0 and NaN take the full sequence, which leaves -0.0 unchanged, as this test would)
+    const long long xb = __double_as_longlong(x);
+    if (xb >= 0 && xb < __double_as_longlong(L)) return x;
     if (!(x > -L && x < L)) x = fmod(x, L);
     if (x < 0.0) x = __dadd_rn(x, L);
     if (x >= L) x = __dadd_rn(x, -L);
@@ -356,9 +359,11 @@ __global__ void k_work_count(const uint32_t *__restrict__ cell_start, int n_cell
 }
 
 // Work item w = (cell, first slot): work[2w] = cell, work[2w+1] = slot.  Its cost estimate is
-// (particles in the item) x (particles in the 27 neighbour cells); the sort key is the top 16
-// bits of that cost as an FP32 number, inverted, so that an ascending sort puts the most
-// expensive items first.  Unused entries keep the key 0xFFFFFFFF and sort last.
+// (particles in the item) x (particles in the 27 neighbour cells); the sort key is its class
+// log2(cost) to 1/8 octave (the FP32 exponent and top 3 mantissa bits, 8 bits), inverted, so
+// that one 8-bit pass of the stable sort puts the most expensive items first.  Unused entries
+// keep the key 0xFFFFFFFF (low byte 255, the cheapest class) and, being after every used entry,
+// stay last.
 __global__ void k_work_fill(const uint32_t *__restrict__ cell_start,
                             const uint32_t *__restrict__ work_off, int n_c,
                             uint32_t *__restrict__ work, uint32_t *__restrict__ work_key,
@@ -382,7 +387,9 @@ __global__ void k_work_fill(const uint32_t *__restrict__ cell_start,
             work[2 * (size_t)w] = (uint32_t)c;
             work[2 * (size_t)w + 1] = i;
             const float cost = (float)min((uint32_t)P3M_PAIR_TI, e - i) * nb;
-            work_key[w] = 0xFFFFu - (__float_as_uint(cost) >> 16);
+            // 8-bit cost class: log2(cost) to 1/8 octave (cost >= 1), largest first
+            const uint32_t cls = (__float_as_uint(cost) >> 20) - (127u << 3);
+            work_key[w] = 255u - min(cls, 255u);
             work_val[w] = w;
         }
     }
@@ -511,7 +518,7 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     if (e != cudaSuccess) return e;
     // most expensive work items first (longest-processing-time order for the pair kernel)
     uint32_t *k[2] = {c->work_key, c->work_key_alt}, *v[2] = {c->work_order, c->work_order_alt};
-    e = radix_sort_pairs(k, v, false, (int64_t)c->max_work, 16, c->digit_counts, c->scan_aux,
+    e = radix_sort_pairs(k, v, false, (int64_t)c->max_work, 8, c->digit_counts, c->scan_aux,
                          c->stream, &c->launches);
     c->work_key = k[0];
     c->work_key_alt = k[1];
