@@ -28,7 +28,8 @@
  *     z.  Caller arrays are borrowed for the duration of the call only.
  *   - on_device != 0: the pointers are CUDA device pointers on the current device; the call
  *     returns with the work queued on the context's stream (host arrays: the call returns
- *     after the copies completed).
+ *     after the copies completed).  Page-locked (pinned) host arrays are read and written in
+ *     place by the kernels over the CPU-GPU link; other host arrays are staged through copies.
  *   - The context owns all device memory, cuFFT plans and events; p3m_free releases them.
  *   - Particle order: the library keeps particles sorted by chaining cell internally; every
  *     array a caller reads back is in the caller's original order (the order of

@@ -640,6 +640,23 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
     return P3M_OK;
 }
 
+namespace {
+
+// The device address of page-locked (pinned) host memory, or NULL for any other pointer: the
+// kernels then read or write it directly over the CPU-GPU link instead of staging it through
+// a separate copy.
+const void *pinned_view(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // older runtimes report unregistered memory as an error
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+}  // namespace
+
 extern "C" int p3m_set_particles(p3m_ctx *c, const double *pos, const double *mom,
                                  const double *acc, double mass, double a, int on_device)
 {
@@ -650,15 +667,21 @@ extern "C" int p3m_set_particles(p3m_ctx *c, const double *pos, const double *mo
     const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
     CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(uint32_t), c->stream));
     const double *sp = pos, *sm = mom, *sa = acc;
-    if (!on_device) {
-        CK(cudaMemcpyAsync(c->pos_alt, pos, bytes, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(c->mom_alt, mom, bytes, cudaMemcpyHostToDevice, c->stream));
-        sp = c->pos_alt;
-        sm = c->mom_alt;
-        if (acc) {
-            CK(cudaMemcpyAsync(c->acc_lr, acc, bytes, cudaMemcpyHostToDevice, c->stream));
-            sa = c->acc_lr;
+    if (!on_device) {  // pinned host arrays are read in place; others are copied first
+        const double *src[3] = {pos, mom, acc};
+        double *stage[3] = {c->pos_alt, c->mom_alt, c->acc_lr};
+        const double *use[3] = {nullptr, nullptr, nullptr};
+        for (int t = 0; t < 3; ++t) {
+            if (!src[t]) continue;
+            use[t] = (const double *)pinned_view(src[t]);
+            if (!use[t]) {
+                CK(cudaMemcpyAsync(stage[t], src[t], bytes, cudaMemcpyHostToDevice, c->stream));
+                use[t] = stage[t];
+            }
         }
+        sp = use[0];
+        sm = use[1];
+        sa = use[2];
     }
     CK(launch_load_particles(c, sp, sm, sa));
     uint32_t flags = 0;
@@ -776,10 +799,16 @@ extern "C" int p3m_get_particles(p3m_ctx *c, double *pos, double *mom, double *a
     const size_t bytes = 3 * sizeof(double) * (size_t)c->g.n;
     double *outs[3] = {pos, mom, acc};
     const double *srcs[3] = {c->pos, c->mom, c->acc};
+    bool inv_ready = false;  // pid_alt is free between sorts: the inverse permutation
     for (int t = 0; t < 3; ++t) {
         if (!outs[t]) continue;
+        double *direct = on_device ? nullptr : (double *)pinned_view(outs[t]);
         if (on_device) {
             CK(launch_scatter_out(c, srcs[t], outs[t]));
+        } else if (direct) {  // pinned host array: written in place, sequentially
+            if (!inv_ready) CK(launch_inverse_pid(c, c->pid_alt));
+            inv_ready = true;
+            CK(launch_gather_out(c, srcs[t], c->pid_alt, direct));
         } else {
             double *stage = t == 0 ? c->pos_alt : (t == 1 ? c->mom_alt : c->acc_lr);
             CK(launch_scatter_out(c, srcs[t], stage));

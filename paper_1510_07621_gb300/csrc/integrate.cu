@@ -78,6 +78,28 @@ __global__ void k_scatter(const double *__restrict__ src, const uint32_t *__rest
     }
 }
 
+// inv[pid[k]] = k: the slot of each particle of the caller's order.
+__global__ void k_inverse(const uint32_t *__restrict__ pid, int64_t n, uint32_t *__restrict__ inv)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        inv[pid[k]] = (uint32_t)k;
+}
+
+// dst (caller order) = src (slot order) through the inverse permutation: the writes are
+// sequential, so dst may be host memory that the GPU writes over the CPU-GPU link.
+__global__ void k_gather_out(const double *__restrict__ src, const uint32_t *__restrict__ inv,
+                             int64_t n, double *__restrict__ dst)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = inv[j];
+        dst[j] = src[k];
+        dst[n + j] = src[n + k];
+        dst[2 * n + j] = src[2 * n + k];
+    }
+}
+
 // Per-block partial sums of (px, py, pz, |p|^2) in a fixed order; then one block adds the
 // partials in block order.  Same result on every run.
 constexpr int kRedThreads = 256;
@@ -191,6 +213,20 @@ cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst)
 {
     c->launches += 1;
     k_scatter<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(src, c->pid, c->g.n, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inverse_pid(p3m_ctx *c, uint32_t *inv)
+{
+    c->launches += 1;
+    k_inverse<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(c->pid, c->g.n, inv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_out(p3m_ctx *c, const double *src, const uint32_t *inv, double *dst)
+{
+    c->launches += 1;
+    k_gather_out<<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(src, inv, c->g.n, dst);
     return cudaGetLastError();
 }
 

@@ -281,6 +281,9 @@ cudaError_t launch_axpy(p3m_ctx *c, double *y, const double *x, double alpha);
 cudaError_t launch_load_particles(p3m_ctx *c, const double *pos, const double *mom,
                                   const double *acc);
 cudaError_t launch_scatter_out(p3m_ctx *c, const double *src, double *dst);
+// inv[pid[k]] = k, then dst[j] = src[inv[j]] (3 x n): caller order with sequential writes
+cudaError_t launch_inverse_pid(p3m_ctx *c, uint32_t *inv);
+cudaError_t launch_gather_out(p3m_ctx *c, const double *src, const uint32_t *inv, double *dst);
 cudaError_t launch_diag(p3m_ctx *c, double *host_out /* [4]: px py pz 2*kinetic*m*a^2 */);
 
 // ------------------------------------------------------------------ launchers (adjoint.cu)

@@ -313,3 +313,33 @@ def test_fma_probe_reports_plausible_rates(P3M):
     f32, f64 = measure_fma_peak(False), measure_fma_peak(True)
     assert 1.0 < f32 < 161.0
     assert 0.01 < f64 < f32
+
+
+def test_pinned_host_arrays_match_pageable_ones(P3M):
+    """Page-locked host arrays are read and written in place by the kernels (over the CPU-GPU
+    link); the results equal those of pageable arrays, which are staged through copies."""
+    torch = pytest.importorskip("torch")
+    pos, mom, kw = _case("clustered48")
+    n = pos.shape[1]
+    res = []
+    for pinned in (False, True):
+        with P3M(kw["box"], n, kw["mesh"], precision="fp64") as sim:
+            if pinned:
+                hp = torch.from_numpy(pos.copy()).pin_memory()
+                hm = torch.from_numpy(mom.copy()).pin_memory()
+                sim.set_particles(hp, hm, a=0.5)
+                sim.step(0.5, 0.01)
+                op = torch.empty((3, n), dtype=torch.float64).pin_memory()
+                om = torch.empty((3, n), dtype=torch.float64).pin_memory()
+                oa = torch.empty((3, n), dtype=torch.float64).pin_memory()
+                sim.get_particles(op, om, oa)
+                res.append((op.numpy().copy(), om.numpy().copy(), oa.numpy().copy()))
+            else:
+                sim.set_particles(pos, mom, a=0.5)
+                sim.step(0.5, 0.01)
+                op, om = np.empty((3, n)), np.empty((3, n))
+                oa = np.empty((3, n))
+                sim.get_particles(op, om, oa)
+                res.append((op, om, oa))
+    for x, y in zip(res[0], res[1]):
+        assert np.max(np.abs(x - y)) <= 1e-12 * max(1.0, np.max(np.abs(x)))
