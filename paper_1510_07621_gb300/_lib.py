@@ -84,6 +84,7 @@ SIGNATURES = {
     "p3m_ensemble_free": (None, [_vp]),
     "p3m_ensemble_set_batched": (_c.c_int, [_vp, _c.c_int]),
     "p3m_autotune": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _vp]),
+    "p3m_get_tuning": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "p3m_cell_sort_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_double, _c.c_int, _c.c_int,
                                          _vp, _vp, _vp, _vp]),
     "p3m_measure_fma_peak": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_double)]),

@@ -474,8 +474,50 @@ extern "C" int p3m_autotune(p3m_ctx *c, int *sub_bits_out, double *ms_out)
     int rc = key_current(c);
     if (!rc) rc = evaluate(c, 0.0, nullptr);
     if (rc) return rc;
+    // then the FP32 pair kernel's tile length at that key (2 or 4 blocks of 32 j particles)
+    if (c->precision == P3M_PREC_MIXED && c->short_range) {
+        double best_t = 1e300;
+        int best_tb = c->tile_blocks;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int tb = 2; tb <= 4; tb += 2) {
+            c->tile_blocks = tb;
+            rc = key_current(c);
+            if (!rc) rc = evaluate(c, 0.0, nullptr);  // warm-up
+            if (rc) return rc;
+            CK(cudaEventRecord(e0, c->stream));
+            for (int r = 0; r < 2 && !rc; ++r) {
+                rc = key_current(c);
+                if (!rc) rc = evaluate(c, 0.0, nullptr);
+            }
+            if (rc) return rc;
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_t) {
+                best_t = ms;
+                best_tb = tb;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->tile_blocks = best_tb;
+        ++c->geom_version;  // captured graphs bake the kernel choice
+        rc = key_current(c);
+        if (!rc) rc = evaluate(c, 0.0, nullptr);
+        if (rc) return rc;
+    }
     c->forces_valid = true;
     if (sub_bits_out) *sub_bits_out = best_b;
+    return P3M_OK;
+}
+
+extern "C" int p3m_get_tuning(const p3m_ctx *c, int *sub_bits, int *tile_blocks)
+{
+    if (!c) return P3M_EINVAL;
+    if (sub_bits) *sub_bits = c->g.sub_bits;
+    if (tile_blocks) *tile_blocks = c->tile_blocks;
     return P3M_OK;
 }
 

@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kTJ = P3M_PAIR_TJ;  // 128
 constexpr int kBlocksPerTile = kTJ / 32;
-constexpr int kBlocksPerTileX2 = 4;  // FP32 kernel: 128 j particles (1.5 KB) per tile
+constexpr int kMaxBlocksPerTileX2 = 4;  // FP32 kernel: up to 128 j particles (1.5 KB) per tile
 
 // Coefficients of the FP64 split factor (the context's gpoly64): g = 1 + r^3 sum_k c[k] tau^k
 // (k <= P3M_SPLIT_DEG64), tau = r^2 c[P3M_SPLIT_DEG64 + 1] - 1.
@@ -312,7 +312,7 @@ __device__ __forceinline__ f2 pair_factor2(f2 r2, const PairConst2 &k)
     return f2_mul(gval, s3);
 }
 
-template <bool kBatched>
+template <bool kBatched, int kTileBlocks>
 __global__ void __launch_bounds__(32, 32)
     k_pairs_x2(PairArgs a0, const PairArgs *__restrict__ descs, const uint32_t *__restrict__ order,
                const uint32_t *__restrict__ n_work_ptr, uint32_t *__restrict__ cursor)
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(32, 32)
     constexpr int kBlockFloats = 96;  // x[32] y[32] z[32]
     constexpr int kArgWords = sizeof(PairArgs) / 8;
     static_assert(sizeof(PairArgs) % 8 == 0, "PairArgs is copied in 8-byte words");
-    __shared__ __align__(128) float sj[2][kBlocksPerTileX2 * kBlockFloats];
+    __shared__ __align__(128) float sj[2][kTileBlocks * kBlockFloats];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ NeighbourF nbr[27];
     __shared__ __align__(16) PairArgs sA;  // the current work item's context
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(32, 32)
             }
         };
         auto issue = [&](int nb, uint32_t b, int to) {
-            const uint32_t bend = min(b + kBlocksPerTileX2, (nbr[nb].end + 31) >> 5);
+            const uint32_t bend = min(b + kTileBlocks, (nbr[nb].end + 31) >> 5);
             const uint32_t bytes = (bend - b) * (uint32_t)(kBlockFloats * sizeof(float));
             mbar_expect_tx(&bar[to], bytes);
             bulk_load(&sj[to][0], relx + (size_t)b * kBlockFloats, bytes, &bar[to]);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(32, 32)
         if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
         while (nb_c < 27) {
             const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
-            const uint32_t bend = min(b_c + kBlocksPerTileX2, (nend + 31) >> 5);
+            const uint32_t bend = min(b_c + kTileBlocks, (nend + 31) >> 5);
             int nb_n = nb_c;
             uint32_t b_n = bend;
             next_tile(nb_n, b_n);
@@ -631,13 +631,14 @@ cudaError_t pairs_x2_impl(p3m_ctx *c, const double *acc_in, double *acc_out, dou
     cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
     cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);  // last evaluation
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2<false>, 32, 0);
+    auto kern = c->tile_blocks == 2 ? k_pairs_x2<false, 2> : k_pairs_x2<false, kMaxBlocksPerTileX2>;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     c->launches += 1;
-    k_pairs_x2<false><<<c->num_sms * per_sm, 32, 0, c->stream>>>(
-        pair_args(c, acc_in, acc_out, kfac, kfac_dev), nullptr, c->work_order,
-        c->work_off + c->g.n_cells, c->counters);
+    kern<<<c->num_sms * per_sm, 32, 0, c->stream>>>(pair_args(c, acc_in, acc_out, kfac, kfac_dev),
+                                                    nullptr, c->work_order,
+                                                    c->work_off + c->g.n_cells, c->counters);
     return cudaGetLastError();
 }
 
@@ -699,12 +700,14 @@ cudaError_t launch_pairs_batched(const PairArgs *descs, const uint32_t *order,
     cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2<true>, 32, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_x2<true, kMaxBlocksPerTileX2>,
+                                                      32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     PairArgs unused;
     memset(&unused, 0, sizeof(unused));
-    k_pairs_x2<true><<<num_sms * per_sm, 32, 0, s>>>(unused, descs, order, n_total, cursor);
+    k_pairs_x2<true, kMaxBlocksPerTileX2><<<num_sms * per_sm, 32, 0, s>>>(unused, descs, order,
+                                                                          n_total, cursor);
     return cudaGetLastError();
 }
 
