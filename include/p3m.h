@@ -233,10 +233,10 @@ int p3m_ensemble_set_batched(p3m_ensemble *ens, int enable);
  * Autotuner of the sort key's Morton depth and of the FP32 pair kernel's tile length: times two
  * force evaluations of the current particles for each sub_bits in 0..3 whose key fits in 32 bits
  * (ms_out[b], nullable; NaN when skipped), keeps the fastest (*sub_bits_out), then (FP32 P3M
- * contexts) times tiles of 2 and 4 blocks of 32 j particles at that depth and keeps the faster,
+ * contexts) times tiles of 3 and 5 blocks of 32 j particles at that depth and keeps the faster,
  * and leaves valid forces.  The cells, and hence which pairs interact, do not depend on either
  * choice; the forces agree up to the FP32 rounding of a different summation order.
- * p3m_get_tuning reports the current choices (tile_blocks: 2 or 4).
+ * p3m_get_tuning reports the current choices (tile_blocks: 3 or 5; 5 by default).
  */
 int p3m_autotune(p3m_ctx *ctx, int *sub_bits_out, double *ms_out);
 int p3m_get_tuning(const p3m_ctx *ctx, int *sub_bits, int *tile_blocks);

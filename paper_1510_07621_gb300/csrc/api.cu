@@ -476,7 +476,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
     if (!c) return fail(nullptr, P3M_ENOMEM, "p3m_init: host allocation failed");
     c->g = g;
     c->precision = opt.precision;
-    c->tile_blocks = 4;
+    c->tile_blocks = 5;
     c->deconvolve = opt.deconvolve_cic ? 1 : 0;
     c->short_range = opt.short_range ? 1 : 0;
     c->cosmo = cs;

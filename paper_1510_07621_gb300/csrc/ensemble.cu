@@ -474,13 +474,13 @@ extern "C" int p3m_autotune(p3m_ctx *c, int *sub_bits_out, double *ms_out)
     int rc = key_current(c);
     if (!rc) rc = evaluate(c, 0.0, nullptr);
     if (rc) return rc;
-    // then the FP32 pair kernel's tile length at that key (2 or 4 blocks of 32 j particles)
+    // then the FP32 pair kernel's tile length at that key (3 or 5 blocks of 32 j particles)
     if (c->precision == P3M_PREC_MIXED && c->short_range) {
         double best_t = 1e300;
         int best_tb = c->tile_blocks;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int tb = 2; tb <= 4; tb += 2) {
+        for (int tb = 3; tb <= 5; tb += 2) {
             c->tile_blocks = tb;
             rc = key_current(c);
             if (!rc) rc = evaluate(c, 0.0, nullptr);  // warm-up

@@ -9,7 +9,7 @@
 //
 // Layout of the work: a CTA is one warp and a work item is up to 32 particles of one cell (one
 // per lane).  The warp streams the j particles of the 27 neighbour cells through shared memory
-// in tiles of up to four 32-slot blocks of the sorted order, copied by the bulk-copy (TMA)
+// in tiles of up to five 32-slot blocks of the sorted order, copied by the bulk-copy (TMA)
 // engine into two alternating buffers (the next tile in flight while the current one is used;
 // one mbarrier per buffer; every wait bounded).  The warp skips a block when no lane's particle
 // is within r_c of the block's bounding box, evaluates it without per-pair tests when the box
@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "p3m_device.cuh"
 #include "p3m_internal.cuh"
@@ -35,7 +36,8 @@ namespace {
 
 constexpr int kTJ = P3M_PAIR_TJ;  // 128
 constexpr int kBlocksPerTile = kTJ / 32;
-constexpr int kMaxBlocksPerTileX2 = 4;  // FP32 kernel: up to 128 j particles (1.5 KB) per tile
+constexpr int kMaxBlocksPerTileX2 = 5;  // FP32 kernel: up to 160 j particles (1.9 KB) per tile
+constexpr int kShortTileX2 = 3;        // the autotuner's other choice
 
 // Coefficients of the FP64 split factor (the context's gpoly64): g = 1 + r^3 sum_k c[k] tau^k
 // (k <= P3M_SPLIT_DEG64), tau = r^2 c[P3M_SPLIT_DEG64 + 1] - 1.
@@ -282,7 +284,8 @@ __global__ void __launch_bounds__(32)
 // r^2 starts its sum at kTiny = 1e-20: a pair at r = 0 (the particle itself, or a coincident
 // one) then gets a finite factor, and its contribution f * d is exactly 0 without a select;
 // for r^2 > 1e-12 the addend is absorbed by FP32 rounding.  Pairs are counted when
-// kTiny < r^2 < r_c^2.
+// kTiny < r^2 < r_c^2 (the kTiny test is made in the own cell only, the one place where r^2 can
+// be exactly kTiny).
 
 constexpr float kTiny = 1e-20f;
 
@@ -386,8 +389,9 @@ __global__ void __launch_bounds__(32, 32)
         __syncwarp();  // the previous item is done with nbr
         if (lane < 27) nbr[lane] = make_neighbour(g, A.cell_start, cx, cy, cz, lane);
         __syncwarp();
-        unsigned long long my_pairs = 0, st_fast = 0, st_tested = 0, st_eval = 0, st_culled = 0,
-                           st_tiles = 0, st_empty_tiles = 0;
+        // the item's pair count (this lane) and work counters (warp-uniform)
+        uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0, n_culled = 0, n_tiles = 0,
+                 n_empty = 0;
 
         const uint32_t i = first + lane;
         const bool valid = i < cend;
@@ -417,6 +421,10 @@ __global__ void __launch_bounds__(32, 32)
         next_tile(nb_c, b_c);
         int buf = 0;
         if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
+        // x_i in the current neighbour cell's frame, set when the tile walk enters the cell
+        int nb_frame = -1;
+        f2 xs2 = 0, ys2 = 0, zs2 = 0;
+        float cxs = 0.0f, cys = 0.0f, czs = 0.0f;
         while (nb_c < 27) {
             const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
             const uint32_t bend = min(b_c + kTileBlocks, (nend + 31) >> 5);
@@ -432,18 +440,52 @@ __global__ void __launch_bounds__(32, 32)
                 if (nb_n < 27) mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
                 break;
             }
-            const NeighbourF &q = nbr[nb_c];
-            // x_i in the neighbour cell's frame: (x_i - s) with s = sx + rx
-            const float xs = (xi.x - q.sx) - q.rx;
-            const float ys = (xi.y - q.sy) - q.ry;
-            const float zs = (xi.z - q.sz) - q.rz;
-            const f2 xs2 = f2_pack(xs, xs), ys2 = f2_pack(ys, ys), zs2 = f2_pack(zs, zs);
-            const float cxs = xa - q.imx, cys = ya - q.imy, czs = za - q.imz;
+            if (nb_c != nb_frame) {
+                nb_frame = nb_c;
+                const NeighbourF &q = nbr[nb_c];
+                // x_i in the neighbour cell's frame: (x_i - s) with s = sx + rx
+                const float xs = (xi.x - q.sx) - q.rx;
+                const float ys = (xi.y - q.sy) - q.ry;
+                const float zs = (xi.z - q.sz) - q.rz;
+                xs2 = f2_pack(xs, xs);
+                ys2 = f2_pack(ys, ys);
+                zs2 = f2_pack(zs, zs);
+                cxs = xa - q.imx;
+                cys = ya - q.imy;
+                czs = za - q.imz;
+            }
             f2 px = 0, py = 0, pz = 0;  // bit pattern 0 = (+0.0f, +0.0f)
-            uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0, n_culled = 0;
+            const uint32_t culled0 = n_culled;
+
+            // Pair counts: a pair is counted when kTiny < r^2 < r_c^2.  r^2 = kTiny (all three
+            // FP32 differences zero) happens for the particle itself and for coincident
+            // particles, which always share a cell, so only the own cell (neighbour 13) tests
+            // r^2 > kTiny; elsewhere every pair with r^2 < r_c^2 counts, and an all-inside block
+            // adds its slot count without per-pair tests.
+
+            // the pair (j, j+1) from its packed coordinates in an all-inside block, where every
+            // lane accepts both; lo/hi (warp-uniform): which halves belong to the neighbour cell
+            auto eval_inside = [&](auto own, f2 xj, f2 yj, f2 zj, bool lo, bool hi) {
+                const f2 dx = f2_sub(xj, xs2), dy = f2_sub(yj, ys2), dz = f2_sub(zj, zs2);
+                const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, kc.tiny)));
+                f2 f = pair_factor2(r2, kc);
+                if (!(lo && hi)) {
+                    float fl, fh;
+                    f2_unpack(f, fl, fh);
+                    f = f2_pack(lo ? fl : 0.0f, hi ? fh : 0.0f);
+                }
+                px = f2_fma(f, dx, px);
+                py = f2_fma(f, dy, py);
+                pz = f2_fma(f, dz, pz);
+                if (decltype(own)::value) {
+                    float r2l, r2h;
+                    f2_unpack(r2, r2l, r2h);
+                    cnt += (lo && r2l > kTiny) + (hi && r2h > kTiny);
+                }
+            };
 
             // one aligned pair (p, p+1) of the block at bx; lo/hi: which halves take part
-            auto pair_tested = [&](const float *bx, uint32_t p, bool lo, bool hi) {
+            auto pair_tested = [&](auto own, const float *bx, uint32_t p, bool lo, bool hi) {
                 const f2 dx = f2_sub(*(const f2 *)(bx + p), xs2);
                 const f2 dy = f2_sub(*(const f2 *)(bx + 32 + p), ys2);
                 const f2 dz = f2_sub(*(const f2 *)(bx + 64 + p), zs2);
@@ -459,20 +501,28 @@ __global__ void __launch_bounds__(32, 32)
                 px = f2_fma(f, dx, px);
                 py = f2_fma(f, dy, py);
                 pz = f2_fma(f, dz, pz);
-                cnt += (inl && r2l > kTiny) + (inh && r2h > kTiny);
+                if (decltype(own)::value)
+                    cnt += (inl && r2l > kTiny) + (inh && r2h > kTiny);
+                else
+                    cnt += inl + inh;
             };
 
-            // two aligned pairs (p, p+1) and (p+2, p+3), all four halves taking part: each
+            // four slots p .. p+3 (p a multiple of 4) as two pairs, all halves taking part: each
             // pair is skipped when no lane accepts it, and when both are needed their
             // evaluations interleave
-            auto pairs_tested2 = [&](const float *bx, uint32_t p) {
+            auto pairs_tested2 = [&](auto own, const float *bx, uint32_t p) {
+                const float4 X = *(const float4 *)(bx + p), Y = *(const float4 *)(bx + 32 + p),
+                             Z = *(const float4 *)(bx + 64 + p);
                 f2 d[2][3], r2[2];
                 bool in[2][2], any[2];
+                d[0][0] = f2_sub(f2_pack(X.x, X.y), xs2);
+                d[0][1] = f2_sub(f2_pack(Y.x, Y.y), ys2);
+                d[0][2] = f2_sub(f2_pack(Z.x, Z.y), zs2);
+                d[1][0] = f2_sub(f2_pack(X.z, X.w), xs2);
+                d[1][1] = f2_sub(f2_pack(Y.z, Y.w), ys2);
+                d[1][2] = f2_sub(f2_pack(Z.z, Z.w), zs2);
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    d[u][0] = f2_sub(*(const f2 *)(bx + p + 2 * u), xs2);
-                    d[u][1] = f2_sub(*(const f2 *)(bx + 32 + p + 2 * u), ys2);
-                    d[u][2] = f2_sub(*(const f2 *)(bx + 64 + p + 2 * u), zs2);
                     r2[u] = f2_fma(d[u][2], d[u][2], f2_fma(d[u][1], d[u][1], f2_fma(d[u][0], d[u][0], kc.tiny)));
                     float l, h;
                     f2_unpack(r2[u], l, h);
@@ -486,7 +536,10 @@ __global__ void __launch_bounds__(32, 32)
                     ++n_eval;
                     float l, h;
                     f2_unpack(r2[u], l, h);
-                    cnt += (in[u][0] && l > kTiny) + (in[u][1] && h > kTiny);
+                    if (decltype(own)::value)
+                        cnt += (in[u][0] && l > kTiny) + (in[u][1] && h > kTiny);
+                    else
+                        cnt += in[u][0] + in[u][1];
                     float fl, fh;
                     f2_unpack(pair_factor2(r2[u], kc), fl, fh);
                     const f2 f = f2_pack(in[u][0] ? fl : 0.0f, in[u][1] ? fh : 0.0f);
@@ -496,56 +549,69 @@ __global__ void __launch_bounds__(32, 32)
                 }
             };
 
-            for (uint32_t b = b_c; b < bend; ++b) {
-                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
-                const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
-                const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
-                const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
-                const bool near = valid && ex * ex + ey * ey + ez * ez < rcull2;
-                if (!__any_sync(0xffffffffu, near)) {
-                    ++n_culled;
-                    continue;
-                }
-                const uint32_t j0 = max(b * 32, nstart) - b * 32;  // block-relative range
-                const uint32_t j1 = min(b * 32 + 32, nend) - b * 32;
-                const float *bx = sj[buf] + (b - b_c) * kBlockFloats;
-                const float fx = fmaxf(cxs - lo.x, hi.x - cxs);
-                const float fy = fmaxf(cys - lo.y, hi.y - cys);
-                const float fz = fmaxf(czs - lo.z, hi.z - czs);
-                uint32_t p = j0 & ~1u;
-                if (__all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2)) {
-                    // the block lies within r_c of every particle of the warp
-                    n_fast += j1 - j0;
+            // the blocks of the tile; own: the neighbour is the work item's own cell
+            auto blocks = [&](auto own) {
+                for (uint32_t b = b_c; b < bend; ++b) {
+                    const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                    const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
+                    const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
+                    const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
+                    const bool near = valid && ex * ex + ey * ey + ez * ez < rcull2;
+                    if (!__any_sync(0xffffffffu, near)) {
+                        ++n_culled;
+                        continue;
+                    }
+                    const uint32_t j0 = max(b * 32, nstart) - b * 32;  // block-relative range
+                    const uint32_t j1 = min(b * 32 + 32, nend) - b * 32;
+                    const float *bx = sj[buf] + (b - b_c) * kBlockFloats;
+                    const float fx = fmaxf(cxs - lo.x, hi.x - cxs);
+                    const float fy = fmaxf(cys - lo.y, hi.y - cys);
+                    const float fz = fmaxf(czs - lo.z, hi.z - czs);
+                    uint32_t p = j0 & ~1u;
+                    if (__all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2)) {
+                        // the block lies within r_c of every particle of the warp
+                        n_fast += j1 - j0;
+                        if (!decltype(own)::value) cnt += j1 - j0;
+                        const f2 *px2 = (const f2 *)bx;  // (p, p+1) as one 8-byte load
+                        if ((j0 & 1u) && j0 < j1) {
+                            eval_inside(own, px2[p / 2], px2[16 + p / 2], px2[32 + p / 2], false, true);
+                            p += 2;
+                        }
+                        if ((p & 2u) && p + 1 < j1) {
+                            eval_inside(own, px2[p / 2], px2[16 + p / 2], px2[32 + p / 2], true, true);
+                            p += 2;
+                        }
+                        for (; p + 3 < j1; p += 4) {
+                            const float4 X = *(const float4 *)(bx + p), Y = *(const float4 *)(bx + 32 + p),
+                                         Z = *(const float4 *)(bx + 64 + p);
+                            eval_inside(own, f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y), true, true);
+                            eval_inside(own, f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w), true, true);
+                        }
+                        if (p + 1 < j1) {
+                            eval_inside(own, px2[p / 2], px2[16 + p / 2], px2[32 + p / 2], true, true);
+                            p += 2;
+                        }
+                        if (p < j1) eval_inside(own, px2[p / 2], px2[16 + p / 2], px2[32 + p / 2], true, false);
+                        continue;
+                    }
+                    n_tested += j1 - j0;
                     if ((j0 & 1u) && j0 < j1) {
-                        pair_tested(bx, p, false, true);
+                        pair_tested(own, bx, p, false, true);
                         p += 2;
                     }
-#pragma unroll 2
-                    for (; p + 1 < j1; p += 2) {
-                        const f2 dx = f2_sub(*(const f2 *)(bx + p), xs2);
-                        const f2 dy = f2_sub(*(const f2 *)(bx + 32 + p), ys2);
-                        const f2 dz = f2_sub(*(const f2 *)(bx + 64 + p), zs2);
-                        const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, kc.tiny)));
-                        const f2 f = pair_factor2(r2, kc);
-                        px = f2_fma(f, dx, px);
-                        py = f2_fma(f, dy, py);
-                        pz = f2_fma(f, dz, pz);
-                        float r2l, r2h;
-                        f2_unpack(r2, r2l, r2h);
-                        cnt += (r2l > kTiny) + (r2h > kTiny);
+                    if ((p & 2u) && p + 1 < j1) {
+                        pair_tested(own, bx, p, true, true);
+                        p += 2;
                     }
-                    if (p < j1) pair_tested(bx, p, true, false);
-                    continue;
+                    for (; p + 3 < j1; p += 4) pairs_tested2(own, bx, p);
+                    for (; p + 1 < j1; p += 2) pair_tested(own, bx, p, true, true);
+                    if (p < j1) pair_tested(own, bx, p, true, false);
                 }
-                n_tested += j1 - j0;
-                if ((j0 & 1u) && j0 < j1) {
-                    pair_tested(bx, p, false, true);
-                    p += 2;
-                }
-                for (; p + 3 < j1; p += 4) pairs_tested2(bx, p);
-                for (; p + 1 < j1; p += 2) pair_tested(bx, p, true, true);
-                if (p < j1) pair_tested(bx, p, true, false);
-            }
+            };
+            if (nb_c == 13)
+                blocks(std::true_type{});
+            else
+                blocks(std::false_type{});
             float lo_, hi_;
             f2_unpack(px, lo_, hi_);
             two_sum_add(sax, cax, lo_ + hi_);
@@ -553,13 +619,8 @@ __global__ void __launch_bounds__(32, 32)
             two_sum_add(say, cay, lo_ + hi_);
             f2_unpack(pz, lo_, hi_);
             two_sum_add(saz, caz, lo_ + hi_);
-            if (valid) my_pairs += cnt;
-            st_fast += n_fast;
-            st_tested += n_tested;
-            st_eval += n_eval;
-            st_culled += n_culled;
-            ++st_tiles;
-            if (n_culled == bend - b_c) ++st_empty_tiles;
+            ++n_tiles;
+            if (n_culled - culled0 == bend - b_c) ++n_empty;
             buf ^= 1;
             nb_c = nb_n;
             b_c = b_n;
@@ -582,6 +643,7 @@ __global__ void __launch_bounds__(32, 32)
             }
         }
         // the item's pair count (warp sum) and work counters, into its context
+        unsigned long long my_pairs = valid ? cnt : 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
         if (lane == 0) {
@@ -590,12 +652,12 @@ __global__ void __launch_bounds__(32, 32)
                 atomicAdd(pc, my_pairs);
                 atomicAdd(pc + 1, my_pairs);
             }
-            if (st_fast) atomicAdd(pc + 2, st_fast);
-            if (st_tested) atomicAdd(pc + 3, st_tested);
-            if (st_eval) atomicAdd(pc + 4, 2 * st_eval);
-            if (st_culled) atomicAdd(pc + 5, st_culled);
-            if (st_tiles) atomicAdd(pc + 6, st_tiles);
-            if (st_empty_tiles) atomicAdd(pc + 7, st_empty_tiles);
+            if (n_fast) atomicAdd(pc + 2, (unsigned long long)n_fast);
+            if (n_tested) atomicAdd(pc + 3, (unsigned long long)n_tested);
+            if (n_eval) atomicAdd(pc + 4, 2ull * n_eval);
+            if (n_culled) atomicAdd(pc + 5, (unsigned long long)n_culled);
+            if (n_tiles) atomicAdd(pc + 6, (unsigned long long)n_tiles);
+            if (n_empty) atomicAdd(pc + 7, (unsigned long long)n_empty);
         }
     }
 }
@@ -631,7 +693,8 @@ cudaError_t pairs_x2_impl(p3m_ctx *c, const double *acc_in, double *acc_out, dou
     cudaMemsetAsync(c->counters, 0, sizeof(uint32_t), c->stream);
     cudaMemsetAsync(c->pair_count, 0, sizeof(unsigned long long), c->stream);  // last evaluation
     int per_sm = 0;
-    auto kern = c->tile_blocks == 2 ? k_pairs_x2<false, 2> : k_pairs_x2<false, kMaxBlocksPerTileX2>;
+    auto kern = c->tile_blocks == kShortTileX2 ? k_pairs_x2<false, kShortTileX2>
+                                                : k_pairs_x2<false, kMaxBlocksPerTileX2>;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
