@@ -280,7 +280,7 @@ def run_ours(args, rank, world, local_rank, dist):
     passes = math.ceil(_key_bits(sim) / 8)
     algo_bytes = {  # algorithmic bytes per launch of each HBM-bound phase
         "kick_drift": 124 * n,
-        "sort": (16 + 20 * (passes - 1)) * n,
+        "sort": 16 * passes * n,  # key histogram read (4 B), then per pass key + slot in and out
         "permute": 128 * n,
         "deposit": 32 * n,
         "kspace": 32 * nk,

@@ -54,12 +54,14 @@ struct p3m_ctx {
     void *rel;  // float4 (mixed) or double4 (fp64): position relative to its cell origin
     float4 *block_box;  // per 32-slot block of the sorted order: lo, hi (FP32, absolute)
     float *relx;        // FP32 mode: rel as block-SoA, per 32-slot block x[32] y[32] z[32]
-    int tile_blocks;    // FP32 pair kernel: 32-slot blocks per shared-memory tile (2 or 4)
+    int tile_blocks;    // FP32 pair kernel: 32-slot blocks per shared-memory tile (3 or 5)
 
     // sort
     uint32_t *keys, *keys_alt, *vals, *vals_alt;
     uint32_t *digit_counts;  // 256 * n_tiles
     uint32_t *scan_aux;      // block sums of the scans
+    unsigned long long *sort_status;  // particle sort: 256 look-back entries per 4096-key tile
+    uint32_t *sort_hist;              // particle sort: 4 x 256 digit counts, 4 tile counters
     int n_tiles;
     int key_bits;
     uint32_t *cell_start;  // n_cells + 1

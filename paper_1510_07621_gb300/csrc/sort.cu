@@ -162,6 +162,158 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ------------------------------------------------------------------ one-sweep LSD radix sort
+// The particle sort: one histogram kernel for all passes, then one kernel per 8-bit pass.  A
+// pass's CTAs take 4096-key tiles in launch order from an atomic counter; each ranks its tile
+// (warp w the keys [512 w, 512 w + 512), round by round and lane by lane, so ranks are
+// stable), publishes its per-digit counts, and finds the count of each digit in all earlier
+// tiles by walking back over their published values (decoupled look-back: an entry holds a
+// tile's own count, flag kAgg, or the running total through that tile, flag kInc).  A tile
+// publishes kAgg before it waits for anything, and waits only on tiles taken before it, so
+// every wait ends; each is still bounded (about a second) and sets P3M_FLAG_TIMEOUT when it
+// gives up.  The tile is then reordered in shared memory by digit and written out in runs,
+// coalesced, at global position = (keys of smaller digits) + (keys of the digit in earlier
+// tiles) + (rank in the tile).
+
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpItems = P3M_SORT_TILE / kWarps;  // 512
+constexpr unsigned long long kAgg = 1ull << 62, kInc = 2ull << 62, kCountMask = (1ull << 62) - 1;
+
+// hist[p * 256 + d] += number of keys whose digit p is d, for p < passes (<= 4)
+__global__ void __launch_bounds__(kThreads)
+    k_digit_hist(const uint32_t *__restrict__ keys, int64_t n, int passes, uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t h[4 * kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += kThreads) h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i0 = (int64_t)blockIdx.x * kThreads; i0 < n; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t k = valid ? keys[i] : 0u;
+        for (int p = 0; p < passes; ++p) {
+            const uint32_t d = valid ? (k >> (p * kRadixBits)) & (kRadix - 1) : (uint32_t)kRadix;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p * kRadix + d], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads)
+        if (h[i]) atomicAdd(hist + i, h[i]);
+}
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total);
+
+__global__ void __launch_bounds__(kThreads)
+    k_onesweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t n,
+               int shift, const uint32_t *__restrict__ hist, unsigned long long *status,
+               uint32_t *tile_counter, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+               uint32_t *flags)
+{
+    __shared__ uint32_t s_key[P3M_SORT_TILE];
+    __shared__ uint32_t s_val[P3M_SORT_TILE];
+    __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts, then offsets
+    __shared__ uint32_t s_off[kRadix];           // first tile slot of each digit
+    __shared__ uint32_t s_out[kRadix];           // global position of the digit's first key
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s_wcnt[w][tid] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t wbase = (int64_t)tile * P3M_SORT_TILE + (int64_t)warp * kWarpItems;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    // rank within the warp's 512 keys
+    uint32_t key[kItems], val[kItems], rank[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t idx = wbase + r * 32 + lane;
+        const bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+        const uint32_t d = valid ? (key[r] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int lead = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (valid && lane == lead) {
+            before = s_wcnt[warp][d];
+            s_wcnt[warp][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xffffffffu, before, lead);
+        rank[r] = before + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // thread tid = digit d: the tile's count, published at once; per-warp offsets
+    const int d = tid;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = cnt;
+        cnt += c;
+    }
+    unsigned long long *mine = status + (size_t)tile * kRadix + d;
+    if (tile == 0)
+        atomicExch(mine, kInc | cnt);
+    else
+        atomicExch(mine, kAgg | cnt);
+    s_off[d] = block_exclusive_scan(cnt, nullptr);
+    const uint32_t first = block_exclusive_scan(hist[d], nullptr);
+    // keys of digit d in the tiles before this one
+    unsigned long long before = 0;
+    if (tile > 0) {
+        long long t = (long long)tile - 1;
+        const long long t0 = clock64();
+        for (;;) {
+            const unsigned long long v = *(volatile unsigned long long *)(status + (size_t)t * kRadix + d);
+            const unsigned long long f = v & ~kCountMask;
+            if (f == 0ull) {
+                if (clock64() - t0 > (1ll << 31)) {
+                    atomicOr(flags, P3M_FLAG_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            before += v & kCountMask;
+            if (f == kInc) break;
+            --t;
+        }
+        atomicExch(mine, kInc | (before + cnt));
+    }
+    s_out[d] = first + (uint32_t)before;
+    __syncthreads();
+
+    // the tile in digit order in shared memory, then written out in runs
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t idx = wbase + r * 32 + lane;
+        if (idx < n) {
+            const uint32_t dd = (key[r] >> shift) & (kRadix - 1);
+            const uint32_t slot = s_off[dd] + s_wcnt[warp][dd] + rank[r];
+            s_key[slot] = key[r];
+            s_val[slot] = val[r];
+        }
+    }
+    __syncthreads();
+    const int64_t left = n - (int64_t)tile * P3M_SORT_TILE;
+    const int count = left < P3M_SORT_TILE ? (int)left : P3M_SORT_TILE;
+    for (int j = tid; j < count; j += kThreads) {
+        const uint32_t k = s_key[j];
+        const uint32_t dd = (k >> shift) & (kRadix - 1);
+        const uint32_t p = s_out[dd] + (uint32_t)j - s_off[dd];
+        if (p < n) {  // (always, unless a look-back wait gave up)
+            kout[p] = k;
+            vout[p] = s_val[j];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ exclusive scan (uint32)
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
@@ -464,11 +616,49 @@ cudaError_t radix_sort_pairs(uint32_t **k, uint32_t **v, bool identity_vals, int
     return cudaGetLastError();
 }
 
+// The particle sort (values: the input slots), one-sweep passes; k[0]/v[0] hold the result.
+cudaError_t radix_sort_onesweep(p3m_ctx *c, uint32_t **k, uint32_t **v)
+{
+    const int64_t n = c->g.n;
+    const int passes = (c->key_bits + kRadixBits - 1) / kRadixBits;
+    const unsigned n_tiles = (unsigned)((n + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
+    cudaStream_t s = c->stream;
+    // sort_hist: 4 x 256 digit counts, then one tile counter per pass
+    cudaError_t e = cudaMemsetAsync(c->sort_hist, 0, sizeof(uint32_t) * (4 * kRadix + 4), s);
+    if (e != cudaSuccess) return e;
+    const unsigned hist_grid = (unsigned)min((int64_t)n_tiles, (int64_t)c->num_sms * 4);
+    k_digit_hist<<<hist_grid, kThreads, 0, s>>>(k[0], n, passes, c->sort_hist);
+    c->launches += 1;
+    uint32_t *kin = k[0], *kout = k[1], *vin = nullptr, *vout = v[0];
+    for (int p = 0; p < passes; ++p) {
+        e = cudaMemsetAsync(c->sort_status, 0, sizeof(unsigned long long) * kRadix * n_tiles, s);
+        if (e != cudaSuccess) return e;
+        k_onesweep<<<n_tiles, kThreads, 0, s>>>(kin, vin, n, p * kRadixBits, c->sort_hist + p * kRadix,
+                                                c->sort_status, c->sort_hist + 4 * kRadix + p, kout,
+                                                vout, c->counters + 1);
+        c->launches += 1;
+        uint32_t *t = kin;  // the next pass reads what this one wrote
+        kin = kout;
+        kout = t;
+        uint32_t *vt = vin;
+        vin = vout;
+        vout = vt ? vt : v[1];
+    }
+    if (kin != k[0]) {
+        k[1] = k[0];
+        k[0] = kin;
+    }
+    if (vin != v[0]) {
+        v[1] = v[0];
+        v[0] = vin;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_radix_sort(p3m_ctx *c)
 {
     uint32_t *k[2] = {c->keys, c->keys_alt}, *v[2] = {c->vals, c->vals_alt};
-    cudaError_t e = radix_sort_pairs(k, v, true, c->g.n, c->key_bits, c->digit_counts, c->scan_aux,
-                                     c->stream, &c->launches);
+    cudaError_t e = radix_sort_onesweep(c, k, v);
     c->keys = k[0];
     c->keys_alt = k[1];
     c->vals = v[0];
