@@ -236,7 +236,7 @@ struct V4Of<float> {
 };
 template <>
 struct V4Of<double> {
-    using type = double4;
+    using type = double4_16a;
 };
 
 // FP64 mode: one warp per work item (up to 32 particles of one cell, most expensive items first),
@@ -245,7 +245,7 @@ struct V4Of<double> {
 // pair tests when it lies within r_c of every lane's particle; j data read through the cache
 // and broadcast by shuffles.  out_k += Gm sum_j J(d_kj) (v_j - v_k).
 __global__ void __launch_bounds__(32)
-    k_pairs_vjp64(const double4 *__restrict__ rel, const double *__restrict__ pos,
+    k_pairs_vjp64(const double4_16a *__restrict__ rel, const double *__restrict__ pos,
                   const float4 *__restrict__ block_box, const double *__restrict__ vs,
                   const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ work,
                   const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_work_ptr,
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(32)
         const uint32_t i = first + lane;
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
-        const double4 xi = rel[ii];
+        const double4_16a xi = rel[ii];
         const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];
         const double vix = vs[ii], viy = vs[n + ii], viz = vs[2 * n + ii];
         double o[3] = {0.0, 0.0, 0.0};
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(32)
                 const uint32_t j0 = max(b * 32, js), j1 = min(b * 32 + 32, je);
                 // the block's particles: one coalesced load, then broadcast lane by lane
                 const uint32_t jl = min(b * 32 + lane, (uint32_t)(n - 1));
-                const double4 ql = rel[jl];
+                const double4_16a ql = rel[jl];
                 const double vlx = vs[jl], vly = vs[n + jl], vlz = vs[2 * n + jl];
                 for (uint32_t j = j0; j < j1; ++j) {
                     const int src = (int)(j - b * 32);
@@ -854,7 +854,7 @@ cudaError_t vjp_pairs(p3m_ctx *c, const double *v_slots, double *out_slots)
             c->counters + 1, out_slots);
     } else {
         k_pairs_vjp64<<<c->num_sms * per_sm, 32, 0, c->stream>>>(
-            (const double4 *)c->rel, c->pos, c->block_box, v_slots, c->cell_start, c->work,
+            (const double4_16a *)c->rel, c->pos, c->block_box, v_slots, c->cell_start, c->work,
             c->work_order, c->work_off + c->g.n_cells, c->g, rcull2, rin2, c->counters + 3,
             out_slots);
     }

@@ -395,7 +395,6 @@ cudaError_t launch_kspace(p3m_ctx *c)
 cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc)
 {
     const int M = c->g.mesh;
-    const size_t nk = (size_t)M * M * (M / 2 + 1);
     const size_t smem = sizeof(double) * (3 * (size_t)n_bins + 1);
     const int grid = c->num_sms * 4;
     const double kf = 2.0 * M_PI / c->g.box;

@@ -51,7 +51,7 @@ struct p3m_ctx {
     uint32_t *pid;
     double *pos_alt, *mom_alt;  // permute targets / staging
     uint32_t *pid_alt;
-    void *rel;  // float4 (mixed) or double4 (fp64): position relative to its cell origin
+    void *rel;  // float4 (mixed) or double4_16a (fp64): position relative to its cell origin
     float4 *block_box;  // per 32-slot block of the sorted order: lo, hi (FP32, absolute)
     float *relx;        // FP32 mode: rel as block-SoA, per 32-slot block x[32] y[32] z[32]
     int tile_blocks;    // FP32 pair kernel: 32-slot blocks per shared-memory tile (3 or 5)

@@ -67,7 +67,7 @@ struct Neighbour {
 };
 
 __global__ void __launch_bounds__(32)
-    k_pairs64(const double4 *__restrict__ rel, const double *__restrict__ pos,
+    k_pairs64(const double4_16a *__restrict__ rel, const double *__restrict__ pos,
             const float4 *__restrict__ block_box, const uint32_t *__restrict__ cell_start,
             const uint32_t *__restrict__ work, const uint32_t *__restrict__ order,
             const uint32_t *__restrict__ n_work_ptr, P3MGeom g, GPoly64 gp, float rcull2, float rin2,
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(32)
             uint32_t *__restrict__ counters, unsigned long long *__restrict__ pair_count)
 {
     if (kfac_dev) kfac = *kfac_dev;  // graph-replayed steps read the factor from the device
-    __shared__ __align__(128) double4 sj[2][kTJ];
+    __shared__ __align__(128) double4_16a sj[2][kTJ];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ Neighbour nbr[27];
 
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(32)
         const uint32_t i = first + lane;
         const bool valid = i < cend;
         const uint32_t ii = valid ? i : first;
-        const double4 xi = rel[ii];
+        const double4_16a xi = rel[ii];
         const double xa = pos[ii], ya = pos[n + ii], za = pos[2 * n + ii];  // absolute, FP64
         double ax = 0.0, ay = 0.0, az = 0.0;
 
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(32)
             const uint32_t bend = min(b + kBlocksPerTile, (nbr[nb].end + 31) >> 5);
             const uint32_t j0 = b * 32;
             const uint32_t j1 = min((uint32_t)n, bend * 32);
-            const uint32_t bytes = (j1 - j0) * (uint32_t)sizeof(double4);
+            const uint32_t bytes = (j1 - j0) * (uint32_t)sizeof(double4_16a);
             mbar_expect_tx(&bar[to], bytes);
             bulk_load(&sj[to][0], rel + j0, bytes, &bar[to]);
         };
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(32)
             const double ix = q.imx, iy = q.imy, iz = q.imz;
             // particle i in the frame of the block boxes (absolute, image removed)
             const float cxs = (float)(xa - q.imx), cys = (float)(ya - q.imy), czs = (float)(za - q.imz);
-            const double4 *tile = sj[buf];
+            const double4_16a *tile = sj[buf];
             double px = 0, py = 0, pz = 0;
             uint32_t cnt = 0, n_fast = 0, n_tested = 0, n_eval = 0, n_culled = 0;
             for (uint32_t b = b_c; b < bend; ++b) {
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(32)
                     n_fast += j1 - j0;
 #pragma unroll 2
                     for (uint32_t j = j0; j < j1; ++j) {
-                        const double4 qj = tile[j];
+                        const double4_16a qj = tile[j];
                         const double dx = (qj.x - xs) + ix, dy = (qj.y - ys) + iy, dz = (qj.z - zs) + iz;
                         const double r2 = dx * dx + dy * dy + dz * dz;
                         const bool in = valid && r2 > 0.0;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(32)
                 }
                 n_tested += j1 - j0;
                 for (uint32_t j = j0; j < j1; ++j) {
-                    const double4 qj = tile[j];
+                    const double4_16a qj = tile[j];
                     const double dx = (qj.x - xs) + ix, dy = (qj.y - ys) + iy, dz = (qj.z - zs) + iz;
                     const double r2 = dx * dx + dy * dy + dz * dz;
                     const bool in = valid && r2 < rc2 && r2 > 0.0;
@@ -680,7 +680,7 @@ cudaError_t pairs64_impl(p3m_ctx *c, const double *acc_in, double *acc_out, doub
     const double rin = c->g.r_c * (1.0 - 1e-4) - c->g.box * 1e-6;
     c->launches += 1;
     k_pairs64<<<grid, 32, 0, c->stream>>>(
-        (const double4 *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
+        (const double4_16a *)c->rel, c->pos, c->block_box, c->cell_start, c->work,
         c->work_order, c->work_off + c->g.n_cells, c->g, gp, (float)(rcull * rcull),
         rin > 0.0 ? (float)(rin * rin) : 0.0f, acc_in, acc_out, c->mom, kfac, kfac_dev,
         c->counters, c->pair_count);

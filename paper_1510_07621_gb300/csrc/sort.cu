@@ -404,9 +404,9 @@ __device__ __forceinline__ float4 make_rel<float4>(double x, double y, double z)
     return make_float4((float)x, (float)y, (float)z, 0.0f);
 }
 template <>
-__device__ __forceinline__ double4 make_rel<double4>(double x, double y, double z)
+__device__ __forceinline__ double4_16a make_rel<double4_16a>(double x, double y, double z)
 {
-    return make_double4(x, y, z, 0.0);
+    return make_double4_16a(x, y, z, 0.0);
 }
 
 // FP32 mode: position minus its cell origin (no FP32 absolute coordinate).  FP64 mode: the
@@ -421,10 +421,10 @@ __device__ __forceinline__ R4 rel_coords(double x, double y, double z, uint32_t 
     return make_rel<R4>(x - __ldg(origin + cx), y - __ldg(origin + cy), z - __ldg(origin + cz));
 }
 template <>
-__device__ __forceinline__ double4 rel_coords<double4>(double x, double y, double z, uint32_t,
+__device__ __forceinline__ double4_16a rel_coords<double4_16a>(double x, double y, double z, uint32_t,
                                                        uint32_t, uint32_t, const double *)
 {
-    return make_double4(x, y, z, 0.0);
+    return make_double4_16a(x, y, z, 0.0);
 }
 
 template <typename R4>
@@ -677,9 +677,9 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
                                                      (float4 *)c->rel, c->block_box, c->relx,
                                                      c->tab_origin);
     else
-        k_permute<double4><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
+        k_permute<double4_16a><<<gb, 256, 0, c->stream>>>(c->vals, c->keys, c->g, c->pos, c->mom,
                                                       c->pid, c->pos_alt, c->mom_alt,
-                                                      c->pid_alt, (double4 *)c->rel, c->block_box,
+                                                      c->pid_alt, (double4_16a *)c->rel, c->block_box,
                                                       nullptr, c->tab_origin);
     double *t = c->pos;
     c->pos = c->pos_alt;

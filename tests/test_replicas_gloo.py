@@ -36,7 +36,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_aggregate_as_weak_scaling():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of this (threaded) test process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for rank in range(world):
