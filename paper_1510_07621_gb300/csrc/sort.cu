@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads)
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total);
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_onesweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t n,
                int shift, const uint32_t *__restrict__ hist, unsigned long long *status,
                uint32_t *tile_counter, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t wbase = (int64_t)tile * P3M_SORT_TILE + (int64_t)warp * kWarpItems;
     const uint32_t lt = (1u << lane) - 1u;
 
-    // rank within the warp's 512 keys
+    // the warp's 512 keys and values (all loads in flight at once), then their ranks
     uint32_t key[kItems], val[kItems], rank[kItems];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
@@ -234,6 +234,10 @@ __global__ void __launch_bounds__(kThreads)
         const bool valid = idx < n;
         key[r] = valid ? kin[idx] : 0u;
         val[r] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const bool valid = wbase + r * 32 + lane < n;
         const uint32_t d = valid ? (key[r] >> shift) & (kRadix - 1) : (uint32_t)kRadix;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const int lead = __ffs(peers) - 1;

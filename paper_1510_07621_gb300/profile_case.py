@@ -7,6 +7,7 @@ Workloads (seeded, synthetic):
   clustered_128  the synthetic clustered 128^3 stand-in snapshot (no evolution)
   uniform_128    128^3 Zel'dovich ICs at a = 0.02 (box 200, mesh 128): near-uniform cells
   eds_32         32^3 Zel'dovich ICs at a = 0.02 (box 64, mesh 32)
+  zeldovich_256  256^3 Zel'dovich ICs at a = 0.5 (box 500, mesh 256): the 512^3 run's density
   zeldovich_512  512^3 Zel'dovich ICs at a = 0.5 (box 1000, mesh 512)
 Prints the per-phase times (CUDA events) of the evaluations.
 """
@@ -30,7 +31,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="evolved_128",
                     choices=["evolved_128", "clustered_128", "uniform_128", "eds_32",
-                             "zeldovich_512"])
+                             "zeldovich_256", "zeldovich_512"])
     ap.add_argument("--evals", type=int, default=2)
     ap.add_argument("--steps", action="store_true", help="time steps instead of force evaluations")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -48,6 +49,9 @@ def main():
     elif args.workload == "eds_32":
         box, n_p, mesh, a = 64.0, 32, 32, 0.02
         pos, mom = S.zeldovich(n_p, box, a, 1511)
+    elif args.workload == "zeldovich_256":
+        box, n_p, mesh, a = 500.0, 256, 256, 0.5
+        pos, mom = S.zeldovich(n_p, box, a, 1514)
     else:
         box, n_p, mesh, a = 1000.0, 512, 512, 0.5
         pos, mom = S.zeldovich(n_p, box, a, 1513)
