@@ -13,6 +13,7 @@
 #include <cufft.h>
 #include <math.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "p3m_device.cuh"
@@ -342,9 +343,19 @@ __global__ void __launch_bounds__(32)
 //   e = exp(-r^2 / (4 r_s^2)),
 // g from the fitted polynomial (g'(x) = -x^2 exp(-x^2/4) / (2 sqrt(pi)) in closed form).  r^2
 // starts at kVjpTiny = 1e-20 like in the force kernel; r = 0 pairs are selected out (their w need
-// not vanish for coincident particles).
+// not vanish for coincident particles).  r^2 = kVjpTiny can only occur in the work item's own
+// cell (the particle itself, coincident particles), so only the own cell tests r^2 > kVjpTiny.
+// Tiles of 3 blocks of coordinates and v (4.5 KB for both buffers) keep 32 CTAs per SM.
 constexpr float kVjpTiny = 1e-20f;
-constexpr int kVjpBlocksPerTile = 4;
+constexpr int kVjpBlocksPerTile = 3;
+
+// 2^x (MUFU); here x in [-7.3, 0], no denormal results
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 struct VjpConst2 {
     f2 c[P3M_SPLIT_DEG + 1];
@@ -369,7 +380,7 @@ __device__ __forceinline__ void pair_jac2(f2 r2, const VjpConst2 &k, f2 &h, f2 &
     const f2 s3 = f2_mul(ss, s);
     h = f2_mul(gval, s3);
     f2_unpack(f2_mul(r2, k.ex2arg), al, ah);  // -r^2 log2(e) / (4 r_s^2)
-    const f2 e = f2_pack(exp2f(al), exp2f(ah));
+    const f2 e = f2_pack(ex2_approx(al), ex2_approx(ah));
     const f2 res3 = f2_mul(f2_mul(r, e), s3);
     hr = f2_fma(res3, k.c1, f2_mul(f2_mul(h, ss), k.m3));  // c1 = -1/(2 sqrt(pi) r_s^3), m3 = -3
 }
@@ -461,6 +472,10 @@ __global__ void __launch_bounds__(32, 32)
         next_tile(nb_c, b_c);
         int buf = 0;
         if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
+        // x_i in the current neighbour cell's frame, set when the tile walk enters the cell
+        int nb_frame = -1;
+        f2 xs2 = 0, ys2 = 0, zs2 = 0;
+        float cxs = 0.0f, cys = 0.0f, czs = 0.0f;
         while (nb_c < 27) {
             const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
             const uint32_t bend = min(b_c + kVjpBlocksPerTile, (nend + 31) >> 5);
@@ -476,42 +491,58 @@ __global__ void __launch_bounds__(32, 32)
                 if (nb_n < 27) mbar_wait_bounded(&bar[buf ^ 1], (parity >> (buf ^ 1)) & 1u);
                 break;
             }
-            const NeighbourF &q = nbr[nb_c];
-            const float xs = (xi.x - q.sx) - q.rx;
-            const float ys = (xi.y - q.sy) - q.ry;
-            const float zs = (xi.z - q.sz) - q.rz;
-            const f2 xs2 = f2_pack(xs, xs), ys2 = f2_pack(ys, ys), zs2 = f2_pack(zs, zs);
-            const float cxs = xa - q.imx, cys = ya - q.imy, czs = za - q.imz;
+            if (nb_c != nb_frame) {
+                nb_frame = nb_c;
+                const NeighbourF &q = nbr[nb_c];
+                const float xs = (xi.x - q.sx) - q.rx;
+                const float ys = (xi.y - q.sy) - q.ry;
+                const float zs = (xi.z - q.sz) - q.rz;
+                xs2 = f2_pack(xs, xs);
+                ys2 = f2_pack(ys, ys);
+                zs2 = f2_pack(zs, zs);
+                cxs = xa - q.imx;
+                cys = ya - q.imy;
+                czs = za - q.imz;
+            }
             f2 ox = 0, oy = 0, oz = 0;
 
-            // pair (p, p+1) of the block; lo/hi: which halves take part; test: r < r_c
-            auto pair_vjp = [&](const float *bx, const float *bv, uint32_t p, bool lo, bool hi,
-                                bool test) {
-                const f2 dx = f2_sub(*(const f2 *)(bx + p), xs2);
-                const f2 dy = f2_sub(*(const f2 *)(bx + 32 + p), ys2);
-                const f2 dz = f2_sub(*(const f2 *)(bx + 64 + p), zs2);
+            // pair (j, j+1) from packed coordinates (x, y, z) and v (u, v, w); lo/hi: which
+            // halves take part; test: r < r_c; own: the work item's own cell (r^2 > kVjpTiny test)
+            auto pair_vjp = [&](auto own, f2 xj, f2 yj, f2 zj, f2 uj, f2 vj, f2 wj, bool lo,
+                                bool hi, bool test) {
+                const f2 dx = f2_sub(xj, xs2), dy = f2_sub(yj, ys2), dz = f2_sub(zj, zs2);
                 const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, kc.tiny)));
                 float r2l, r2h;
                 f2_unpack(r2, r2l, r2h);
-                const bool inl = lo && r2l > kVjpTiny && (!test || r2l < rc2);
-                const bool inh = hi && r2h > kVjpTiny && (!test || r2h < rc2);
+                const bool own_c = decltype(own)::value;
+                const bool inl = lo && (!own_c || r2l > kVjpTiny) && (!test || r2l < rc2);
+                const bool inh = hi && (!own_c || r2h > kVjpTiny) && (!test || r2h < rc2);
                 if (test && !__any_sync(0xffffffffu, inl || inh)) return;
                 f2 h, hr;
                 pair_jac2(r2, kc, h, hr);
-                const f2 wx = f2_sub(*(const f2 *)(bv + p), vix2);
-                const f2 wy = f2_sub(*(const f2 *)(bv + 32 + p), viy2);
-                const f2 wz = f2_sub(*(const f2 *)(bv + 64 + p), viz2);
+                const f2 wx = f2_sub(uj, vix2), wy = f2_sub(vj, viy2), wz = f2_sub(wj, viz2);
                 const f2 dw = f2_fma(dz, wz, f2_fma(dy, wy, f2_mul(dx, wx)));
-                float hl, hh, cl, ch;
-                f2_unpack(h, hl, hh);
-                f2_unpack(f2_mul(hr, dw), cl, ch);
-                const f2 hs = f2_pack(inl ? hl : 0.0f, inh ? hh : 0.0f);
-                const f2 cs = f2_pack(inl ? cl : 0.0f, inh ? ch : 0.0f);
+                f2 hs = h, cs = f2_mul(hr, dw);
+                if (own_c || test || !(lo && hi)) {
+                    float hl, hh, cl, ch;
+                    f2_unpack(hs, hl, hh);
+                    f2_unpack(cs, cl, ch);
+                    hs = f2_pack(inl ? hl : 0.0f, inh ? hh : 0.0f);
+                    cs = f2_pack(inl ? cl : 0.0f, inh ? ch : 0.0f);
+                }
                 ox = f2_fma(cs, dx, f2_fma(hs, wx, ox));
                 oy = f2_fma(cs, dy, f2_fma(hs, wy, oy));
                 oz = f2_fma(cs, dz, f2_fma(hs, wz, oz));
             };
+            // the aligned pair (p, p+1) of the block at bx / bv
+            auto pair_at = [&](auto own, const float *bx, const float *bv, uint32_t p, bool lo,
+                               bool hi, bool test) {
+                const f2 *x2 = (const f2 *)bx, *v2 = (const f2 *)bv;
+                pair_vjp(own, x2[p / 2], x2[16 + p / 2], x2[32 + p / 2], v2[p / 2], v2[16 + p / 2],
+                         v2[32 + p / 2], lo, hi, test);
+            };
 
+            auto blocks = [&](auto own) {
             for (uint32_t b = b_c; b < bend; ++b) {
                 const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
                 const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
@@ -529,17 +560,37 @@ __global__ void __launch_bounds__(32, 32)
                     !__all_sync(0xffffffffu, !valid || fx * fx + fy * fy + fz * fz < rin2);
                 uint32_t p = j0 & ~1u;
                 if ((j0 & 1u) && j0 < j1) {
-                    pair_vjp(bx, bv, p, false, true, true);
+                    pair_at(own, bx, bv, p, false, true, true);
                     p += 2;
                 }
                 if (test) {
-                    for (; p + 1 < j1; p += 2) pair_vjp(bx, bv, p, true, true, true);
+                    for (; p + 1 < j1; p += 2) pair_at(own, bx, bv, p, true, true, true);
                 } else {
-#pragma unroll 2
-                    for (; p + 1 < j1; p += 2) pair_vjp(bx, bv, p, true, true, false);
+                    if ((p & 2u) && p + 1 < j1) {
+                        pair_at(own, bx, bv, p, true, true, false);
+                        p += 2;
+                    }
+                    for (; p + 3 < j1; p += 4) {  // four j: 16-byte loads
+                        const float4 X = *(const float4 *)(bx + p), Y = *(const float4 *)(bx + 32 + p),
+                                     Z = *(const float4 *)(bx + 64 + p);
+                        const float4 U = *(const float4 *)(bv + p), V = *(const float4 *)(bv + 32 + p),
+                                     W = *(const float4 *)(bv + 64 + p);
+                        pair_vjp(own, f2_pack(X.x, X.y), f2_pack(Y.x, Y.y), f2_pack(Z.x, Z.y),
+                                 f2_pack(U.x, U.y), f2_pack(V.x, V.y), f2_pack(W.x, W.y), true, true,
+                                 false);
+                        pair_vjp(own, f2_pack(X.z, X.w), f2_pack(Y.z, Y.w), f2_pack(Z.z, Z.w),
+                                 f2_pack(U.z, U.w), f2_pack(V.z, V.w), f2_pack(W.z, W.w), true, true,
+                                 false);
+                    }
+                    for (; p + 1 < j1; p += 2) pair_at(own, bx, bv, p, true, true, false);
                 }
-                if (p < j1) pair_vjp(bx, bv, p, true, false, true);
+                if (p < j1) pair_at(own, bx, bv, p, true, false, true);
             }
+            };
+            if (nb_c == 13)
+                blocks(std::true_type{});
+            else
+                blocks(std::false_type{});
             float lo_, hi_;
             f2_unpack(ox, lo_, hi_);
             two_sum_add(sox, cox, lo_ + hi_);
