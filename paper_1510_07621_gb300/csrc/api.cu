@@ -517,7 +517,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->keys_alt, 4 * N},   {(void **)&c->vals, 4 * N},
             {(void **)&c->vals_alt, 4 * N},   {(void **)&c->digit_counts, 4 * 256 * (size_t)c->n_tiles},
             {(void **)&c->scan_aux, 4 * (scan_n / P3M_SORT_TILE + 4)},
-            {(void **)&c->sort_status, 8 * 256 * ((N + P3M_SORT_TILE - 1) / P3M_SORT_TILE)},
+            {(void **)&c->sort_status, 8 * 256 * (size_t)c->n_tiles},
             {(void **)&c->sort_hist, 4 * (4 * 256 + 4)},
             {(void **)&c->cell_start, 4 * ((size_t)g.n_cells + 1)},
             {(void **)&c->work, 8 * c->max_work}, {(void **)&c->work_off, 4 * ((size_t)g.n_cells + 1)},

@@ -620,11 +620,12 @@ cudaError_t radix_sort_pairs(uint32_t **k, uint32_t **v, bool identity_vals, int
     return cudaGetLastError();
 }
 
-// The particle sort (values: the input slots), one-sweep passes; k[0]/v[0] hold the result.
-cudaError_t radix_sort_onesweep(p3m_ctx *c, uint32_t **k, uint32_t **v)
+// Stable sort of n (key, value) pairs of the context on the low key_bits bits in one-sweep
+// passes (identity_vals: the values are the input slots); k[0]/v[0] hold the result.
+cudaError_t radix_sort_onesweep(p3m_ctx *c, uint32_t **k, uint32_t **v, bool identity_vals,
+                                int64_t n, int key_bits)
 {
-    const int64_t n = c->g.n;
-    const int passes = (c->key_bits + kRadixBits - 1) / kRadixBits;
+    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
     const unsigned n_tiles = (unsigned)((n + P3M_SORT_TILE - 1) / P3M_SORT_TILE);
     cudaStream_t s = c->stream;
     // sort_hist: 4 x 256 digit counts, then one tile counter per pass
@@ -633,7 +634,8 @@ cudaError_t radix_sort_onesweep(p3m_ctx *c, uint32_t **k, uint32_t **v)
     const unsigned hist_grid = (unsigned)min((int64_t)n_tiles, (int64_t)c->num_sms * 4);
     k_digit_hist<<<hist_grid, kThreads, 0, s>>>(k[0], n, passes, c->sort_hist);
     c->launches += 1;
-    uint32_t *kin = k[0], *kout = k[1], *vin = nullptr, *vout = v[0];
+    uint32_t *kin = k[0], *kout = k[1];
+    uint32_t *vin = identity_vals ? nullptr : v[0], *vout = identity_vals ? v[0] : v[1];
     for (int p = 0; p < passes; ++p) {
         e = cudaMemsetAsync(c->sort_status, 0, sizeof(unsigned long long) * kRadix * n_tiles, s);
         if (e != cudaSuccess) return e;
@@ -662,7 +664,7 @@ cudaError_t radix_sort_onesweep(p3m_ctx *c, uint32_t **k, uint32_t **v)
 cudaError_t launch_radix_sort(p3m_ctx *c)
 {
     uint32_t *k[2] = {c->keys, c->keys_alt}, *v[2] = {c->vals, c->vals_alt};
-    cudaError_t e = radix_sort_onesweep(c, k, v);
+    cudaError_t e = radix_sort_onesweep(c, k, v, true, c->g.n, c->key_bits);
     c->keys = k[0];
     c->keys_alt = k[1];
     c->vals = v[0];
@@ -712,8 +714,7 @@ cudaError_t launch_permute_and_cells(p3m_ctx *c)
     if (e != cudaSuccess) return e;
     // most expensive work items first (longest-processing-time order for the pair kernel)
     uint32_t *k[2] = {c->work_key, c->work_key_alt}, *v[2] = {c->work_order, c->work_order_alt};
-    e = radix_sort_pairs(k, v, false, (int64_t)c->max_work, 8, c->digit_counts, c->scan_aux,
-                         c->stream, &c->launches);
+    e = radix_sort_onesweep(c, k, v, false, (int64_t)c->max_work, 8);
     c->work_key = k[0];
     c->work_key_alt = k[1];
     c->work_order = v[0];
