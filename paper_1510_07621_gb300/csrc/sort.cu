@@ -44,6 +44,22 @@ __device__ __forceinline__ uint32_t fine_index(double x, double inv, int nf)
     return (uint32_t)min(f, nf - 1);
 }
 
+// The same index without FP64 arithmetic in almost every case.  x_f = x truncated to its
+// leading 24 significant bits (bit operations), inv_f = inv rounded to FP32: the FP32 product
+// p = x_f inv_f is within 2^-22 x inv < 2^-22 n_f of x inv, and the correctly rounded FP64
+// product within 2^-53 n_f of it.  So when p lies more than tol = 2^-21 n_f from every
+// integer, floor(p) is floor of the FP64 product; otherwise the FP64 product decides.
+__device__ __forceinline__ uint32_t fine_index_fast(double x, double inv, float inv_f, float tol, int nf)
+{
+    const long long xb = __double_as_longlong(x);
+    const int e = (int)((xb >> 52) & 0x7FF) - 1023 + 127;  // x >= 0: no sign bit
+    const float xf = e >= 1 ? __int_as_float((e << 23) | (int)((xb >> 29) & 0x7FFFFF)) : 0.0f;
+    const float p = xf * inv_f;
+    const float k = truncf(p);
+    if (p - k > tol && p - k < 1.0f - tol) return (uint32_t)min((int)k, nf - 1);
+    return fine_index(x, inv, nf);
+}
+
 __device__ __forceinline__ uint32_t make_key(uint32_t fx, uint32_t fy, uint32_t fz,
                                              const P3MGeom &g)
 {
@@ -57,9 +73,9 @@ __device__ __forceinline__ uint32_t make_key(uint32_t fx, uint32_t fy, uint32_t 
     return (cell << (3 * b)) | code;
 }
 
-// Half kick + drift (optional), periodic wrap, key.  Kick and drift use separately rounded
-// products and sums: p += (m K) a; x += p (D / m).  With fac_dev the two factors are read
-// from fac_dev[0], fac_dev[1] (graph-replayed steps).
+// Half kick + drift (optional), periodic wrap, key.  Kick and drift are one FMA each (a single
+// rounding): p += (m K) a; x += p (D / m).  With fac_dev the two factors are read from
+// fac_dev[0], fac_dev[1] (graph-replayed steps).
 __global__ void k_kick_drift_keys(double *__restrict__ pos, double *__restrict__ mom,
                                   const double *__restrict__ acc, P3MGeom g, int kick_drift,
                                   double kfac, double dfac, uint32_t *__restrict__ keys,
@@ -70,6 +86,7 @@ __global__ void k_kick_drift_keys(double *__restrict__ pos, double *__restrict__
         kfac = fac_dev[0];
         dfac = fac_dev[1];
     }
+    const float inv_f = (float)g.inv_fine, tol = (float)g.n_fine * 0x1p-21f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t f[3];
@@ -77,13 +94,13 @@ __global__ void k_kick_drift_keys(double *__restrict__ pos, double *__restrict__
         for (int d = 0; d < 3; ++d) {
             double x = pos[d * n + i];
             if (kick_drift) {
-                double p = __dadd_rn(mom[d * n + i], __dmul_rn(kfac, acc[d * n + i]));
+                const double p = __fma_rn(kfac, acc[d * n + i], mom[d * n + i]);
                 mom[d * n + i] = p;
-                x = __dadd_rn(x, __dmul_rn(p, dfac));
+                x = __fma_rn(p, dfac, x);
             }
             x = wrap_box(x, g.box);
             pos[d * n + i] = x;
-            f[d] = fine_index(x, g.inv_fine, g.n_fine);
+            f[d] = fine_index_fast(x, g.inv_fine, inv_f, tol, g.n_fine);
         }
         keys[i] = make_key(f[0], f[1], f[2], g);
     }
