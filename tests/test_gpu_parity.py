@@ -100,6 +100,28 @@ def test_keys_order_and_cell_ranges_bit_exact(P3M, case, sub_bits):
     assert np.array_equal(starts.astype(np.int64), O.cell_start(cell[order], p.n_c ** 3))
 
 
+@pytest.mark.parametrize("sub_bits", [3, 5])
+@pytest.mark.parametrize("which", ["clustered", "zeldovich"])
+def test_keys_order_bit_exact_full_size_128(P3M, which, sub_bits):
+    """2.1 M particles: 512 sort tiles, 3 (sub_bits 3) or 4 (sub_bits 5) digit passes, so the
+    tile-to-tile count hand-over of the sort is exercised at the benchmark's size."""
+    if which == "clustered":
+        pos, mom = S.clustered(128, 200.0, 1512)
+    else:
+        pos, mom = S.zeldovich(128, 200.0, 0.02, 1512)
+    n = pos.shape[1]
+    with P3M(200.0, n, 128, sub_bits=sub_bits) as sim:
+        sim.set_particles(pos, mom, a=1.0)
+        sim.forces(1.0)
+        keys, ids, starts = sim.get_cells()
+    p = O.Params(200.0, n, 128, sub_bits=sub_bits)
+    cell, key = O.cell_keys(O.wrap(pos, 200.0), p)
+    order = O.stable_order(key)
+    assert np.array_equal(keys.astype(np.int64), key[order])
+    assert np.array_equal(ids.astype(np.int64), order)
+    assert np.array_equal(starts.astype(np.int64), O.cell_start(cell[order], p.n_c ** 3))
+
+
 def test_positions_wrapped_and_order_preserved(P3M):
     pos, _ = _adversarial()
     n = pos.shape[1]
