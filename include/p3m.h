@@ -223,9 +223,9 @@ void p3m_ensemble_free(p3m_ensemble *ens);
  * evaluates every such context's pair sum in one persistent kernel launch (the contexts'
  * arguments read from a device table).  Other contexts step as before.  Results equal the
  * per-context launches up to the FP32 rounding of the mesh deposit's atomics.  Every step then
- * waits for all contexts' mesh phases before the pair launch, which on the 48-simulation
- * ensemble of 48^3..96^3 particles cost more than the shared launch saved (277 M against 285 M
- * particle-updates/s with graphs); enable = 0 returns to independent per-context branches.
+ * waits for all contexts' mesh phases before the pair launch; on the 48-simulation ensemble of
+ * 48^3..96^3 particles the two are within 1 % of each other (342 M and 340 M particle-updates/s
+ * with graphs).  enable = 0 returns to independent per-context branches.
  */
 int p3m_ensemble_set_batched(p3m_ensemble *ens, int enable);
 
