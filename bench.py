@@ -644,6 +644,11 @@ def run_zeldovich512(args):
         dmom = torch.from_numpy(mom).cuda()
         del pos, mom
         sim.set_particles(dpos, dmom, a=a[0])
+        tuned = None
+        if args.autotune:  # the library's autotuner on the ICs, outside the timed region
+            tuned_b, tuned_ms = sim.autotune()
+            tuned = dict(sim.tuning(), ms_per_sub_bits=[None if not np.isfinite(v) else v
+                                                         for v in tuned_ms])
         torch.cuda.synchronize()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         sim.set_timing(True)
@@ -668,7 +673,8 @@ def run_zeldovich512(args):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": 10,
             "warmup": 0, "ms_per_step": ms_steps / 10, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 forces, f64 positions/momenta",
-            "data": "synthetic", "config": {"workload": Z512_NAME, "particles": n, "mesh": n_p},
+            "data": "synthetic", "config": {"workload": Z512_NAME, "particles": n, "mesh": n_p,
+                                             "tuning": tuned},
             "force_evaluation_ms": ms_force, "phase_ms_total": phases,
             "roofline": {"kernel": "pairs", "bound": "alu", "achieved": achieved,
                          "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
