@@ -361,9 +361,6 @@ def run_ours(args, rank, world, local_rank, dist):
                       "h2d_bytes_per_step": 72 * n, "d2h_bytes_per_step": 72 * n,
                       "api": "p3m_set_particles(host pos, mom, acc) + p3m_step + "
                              "p3m_get_particles(host pos, mom, acc)"}
-        snap_pos, snap_mom = hp.numpy().copy(), hm.numpy().copy()
-    else:
-        snap_pos = snap_mom = None
 
     # ---- all-FP64 GPU mode on the same snapshot, and the force difference between the modes
     if rank == 0 and args.fp64_steps > 0 and args.precision == "mixed":
@@ -396,16 +393,11 @@ def run_ours(args, rank, world, local_rank, dist):
                            "fp64_fma_peak_measured": fma64,
                            "pair_frac_of_fp64_peak": pairs64 * FLOPS_PER_PAIR / (ms64 / 1e3) / 1e12 / fma64,
                            "speedup_mixed_over_fp64": value / world / (n / (ms64 / 1e3))}
-        if snap_pos is None:
-            snap_pos, snap_mom = hp.numpy().copy(), hm.numpy().copy()
 
-    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1 only)
+    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1 only), on the
+    # synthetic clustered a = 1 stand-in snapshot: no oracle input comes from the GPU path
     if rank == 0 and world == 1 and args.cpu_sample > 0:
-        if snap_pos is None:
-            hp = np.empty((3, n))
-            hm = np.empty((3, n))
-            sim.get_particles(hp, hm)
-            snap_pos, snap_mom = hp, hm
+        snap_pos, snap_mom = S.clustered(w["n_p"], w["box"], w["seed"])
         sec, threads, desc = oracle_step_time(snap_pos, snap_mom, args.cpu_sample, 99)
         # the same step with the pair sum on one core (mesh part and kick/drift as measured)
         from oracle import p3m_oracle as O
@@ -425,7 +417,8 @@ def run_ours(args, rank, world, local_rank, dist):
                                   "mesh force and kick/drift as in the multi-core figure"}
         out["cpu_baseline"] = {"value": n / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "one_core": one_core,
-                               "sample": desc + "; on the GPU run's a~1 snapshot",
+                               "sample": desc + "; on the synthetic clustered a=1 stand-in "
+                                                "snapshot of the same size",
                                "seconds_per_step_estimate": sec}
     sim.close()
     return out
