@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(32, 32)
     constexpr int kBlockFloats = 96;
     __shared__ __align__(128) float sj[2][kVjpBlocksPerTile * kBlockFloats];
     __shared__ __align__(128) float sv[2][kVjpBlocksPerTile * kBlockFloats];
+    __shared__ __align__(16) float4 sbox[2][2 * kVjpBlocksPerTile];  // the tile's block boxes
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ NeighbourF nbr[27];
 
@@ -462,9 +463,11 @@ __global__ void __launch_bounds__(32, 32)
         auto issue = [&](int nb, uint32_t b, int to) {
             const uint32_t bend = min(b + kVjpBlocksPerTile, (nbr[nb].end + 31) >> 5);
             const uint32_t bytes = (bend - b) * (uint32_t)(kBlockFloats * sizeof(float));
-            mbar_expect_tx(&bar[to], 2 * bytes);
+            const uint32_t box_bytes = (bend - b) * (uint32_t)(2 * sizeof(float4));
+            mbar_expect_tx(&bar[to], 2 * bytes + box_bytes);
             bulk_load(&sj[to][0], relx + (size_t)b * kBlockFloats, bytes, &bar[to]);
             bulk_load(&sv[to][0], vfx + (size_t)b * kBlockFloats, bytes, &bar[to]);
+            bulk_load(&sbox[to][0], block_box + 2 * (size_t)b, box_bytes, &bar[to]);
         };
 
         int nb_c = 0;
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(32, 32)
 
             auto blocks = [&](auto own) {
             for (uint32_t b = b_c; b < bend; ++b) {
-                const float4 lo = __ldg(block_box + 2 * b), hi = __ldg(block_box + 2 * b + 1);
+                const float4 lo = sbox[buf][2 * (b - b_c)], hi = sbox[buf][2 * (b - b_c) + 1];
                 const float ex = fmaxf(fmaxf(lo.x - cxs, cxs - hi.x), 0.0f);
                 const float ey = fmaxf(fmaxf(lo.y - cys, cys - hi.y), 0.0f);
                 const float ez = fmaxf(fmaxf(lo.z - czs, czs - hi.z), 0.0f);
