@@ -273,13 +273,14 @@ __global__ void __launch_bounds__(32)
 }
 
 // ------------------------------------------------------------------ FP32 mode, packed lanes
-// The FP32 kernel proper.  Same traversal as k_pairs (one-warp CTAs, work items of one cell's
+// The FP32 kernel proper.  Same traversal as k_pairs64 (one-warp CTAs, work items of one cell's
 // particles, 27 neighbour cells streamed through two bulk-copy buffers, block culling and the
 // all-inside fast path), but every lane evaluates two j particles at once with the packed
 // f32x2 arithmetic of sm_100-class GPUs: one instruction issues both halves, so the FP32 pipe
 // rather than instruction issue bounds the loop.  The j coordinates come from the block-SoA
-// copy relx (per 32-slot block x[32] y[32] z[32]), so the pair (j, j+1), j even, is one
-// 8-byte shared-memory load per coordinate.
+// copy relx (per 32-slot block x[32] y[32] z[32]), so the pairs (j, j+1) and (j+2, j+3), j a
+// multiple of 4, are one 16-byte shared-memory load per coordinate; the tile's block bounding
+// boxes travel with it in the same bulk-copy transaction.
 //
 // r^2 starts its sum at kTiny = 1e-20: a pair at r = 0 (the particle itself, or a coincident
 // one) then gets a finite factor, and its contribution f * d is exactly 0 without a select;
