@@ -690,7 +690,7 @@ def main():
                                            "zeldovich512"],
                     default="clustered_128")
     ap.add_argument("--sub-bits", type=int, default=None,
-                    help="Morton bits per axis inside a chaining cell (library default if unset)")
+                    help="Hilbert-curve bits per axis inside a chaining cell (library default if unset)")
     ap.add_argument("--autotune", action="store_true",
                     help="run the library's autotuner (sort-key depth, pair tile length) first")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -78,8 +78,8 @@ typedef struct {
     int deconvolve_cic; /* 1 (default): divide G(k) by W(k)^2                              */
     int short_range;    /* 1 (default): P3M; 0: pure PM ('PM' kick algorithm: no Gaussian
                            filter, no pair sum)                                             */
-    int sub_bits;       /* b in 0..3: each chaining cell is split 2^b per side in the sort key
-                           (Morton order inside the cell); -1 = default (3).  The key
+    int sub_bits;       /* b in 0..5: each chaining cell is split 2^b per side in the sort key
+                           (Hilbert-curve order inside the cell); -1 = default (3).  The key
                            (n_c^3 << 3b) must fit in 32 bits                               */
     void *stream;       /* cudaStream_t for all work of the context; NULL = legacy stream  */
 } p3m_options;
@@ -230,7 +230,7 @@ void p3m_ensemble_free(p3m_ensemble *ens);
 int p3m_ensemble_set_batched(p3m_ensemble *ens, int enable);
 
 /*
- * Autotuner of the sort key's Morton depth and of the FP32 pair kernel's tile length: times two
+ * Autotuner of the sort key's Hilbert depth and of the FP32 pair kernel's tile length: times two
  * force evaluations of the current particles for each sub_bits in 0..3 whose key fits in 32 bits
  * (ms_out[b], nullable; NaN when skipped), keeps the fastest (*sub_bits_out), then (FP32 P3M
  * contexts) times tiles of 3 and 5 blocks of 32 j particles at that depth and keeps the faster,
@@ -299,7 +299,7 @@ int p3m_track_energy(p3m_ctx *ctx, int enable);
 
 /*
  * Sorted views of the last sort (after p3m_forces / p3m_step), for checking:
- *   keys      [n]  sort keys in sorted order: (cell << 3b) | Morton(sub-cell), where
+ *   keys      [n]  sort keys in sorted order: (cell << 3b) | Hilbert(sub-cell), where
  *                  cell = (c_z n_c + c_y) n_c + c_x
  *   ids       [n]  original particle index of each sorted slot
  *   cell_start[n_c^3 + 1] first sorted slot of each chaining cell; last entry n

@@ -126,26 +126,57 @@ def fine_index(pos: np.ndarray, p: Params) -> np.ndarray:
     return np.minimum(f, p.n_fine - 1)
 
 
-def morton3(sx, sy, sz, bits: int):
-    """Interleaves the low `bits` bits of (sx, sy, sz), x in the lowest position."""
-    code = np.zeros_like(sx)
-    for t in range(bits):
-        code |= ((sx >> t) & 1) << (3 * t)
-        code |= ((sy >> t) & 1) << (3 * t + 1)
-        code |= ((sz >> t) & 1) << (3 * t + 2)
-    return code
+def hilbert3(sx, sy, sz, bits: int):
+    """Index of the point (sx, sy, sz), each in [0, 2^bits), along the 3-D Hilbert curve of that
+    order, after Skilling, "Programming the Hilbert curve" (AIP Conf. Proc. 707, 2004): the
+    coordinates are turned into the curve's "transposed" index (undo the excess rotations and
+    reflections level by level, then Gray-encode), whose bits, read level by level with x as
+    the most significant of each triple, form the index.  0 <= index < 8^bits; consecutive
+    indices are face-neighbour points."""
+    x = [np.asarray(sx, dtype=np.int64).copy(), np.asarray(sy, dtype=np.int64).copy(),
+         np.asarray(sz, dtype=np.int64).copy()]
+    if bits == 0:
+        return np.zeros_like(x[0])
+    top = 1 << (bits - 1)
+    q = top
+    while q > 1:  # undo the excess work, level q
+        lowmask = q - 1
+        for i in range(3):
+            hit = (x[i] & q) != 0
+            flipped = x[0] ^ lowmask                    # invert the low bits of x0
+            swap = (x[0] ^ x[i]) & lowmask              # or exchange them with x_i
+            new0 = np.where(hit, flipped, x[0] ^ swap)
+            newi = np.where(hit, x[i], x[i] ^ swap)
+            x[0] = new0
+            if i:
+                x[i] = newi
+        q >>= 1
+    x[1] ^= x[0]  # Gray encode
+    x[2] ^= x[1]
+    t = np.zeros_like(x[0])
+    q = top
+    while q > 1:
+        t = np.where((x[2] & q) != 0, t ^ (q - 1), t)
+        q >>= 1
+    for i in range(3):
+        x[i] ^= t
+    h = np.zeros_like(x[0])
+    for level in range(bits - 1, -1, -1):
+        for i in range(3):
+            h = (h << 1) | ((x[i] >> level) & 1)
+    return h
 
 
 def cell_keys(pos: np.ndarray, p: Params):
     """Chaining-cell id c = (c_z n_c + c_y) n_c + c_x with c_d = f_d >> b, and the sort key
-    (c << 3b) | morton(f_x & (2^b-1), f_y & .., f_z & ..).  Returns (cell, key) as int64."""
+    (c << 3b) | hilbert(f_x & (2^b-1), f_y & .., f_z & ..).  Returns (cell, key) as int64."""
     p.check_cells()
     f = fine_index(pos, p)
     b = p.sub_bits
     c = f >> b
     cell = (c[2] * p.n_c + c[1]) * p.n_c + c[0]
     mask = (1 << b) - 1
-    key = (cell << (3 * b)) | morton3(f[0] & mask, f[1] & mask, f[2] & mask, b)
+    key = (cell << (3 * b)) | hilbert3(f[0] & mask, f[1] & mask, f[2] & mask, b)
     return cell, key
 
 

@@ -224,13 +224,13 @@ class P3M:
         self._check(self._lib.p3m_set_stream(self._ctx, ctypes.c_void_p(s)))
 
     def tuning(self) -> dict:
-        """Current sort-key Morton depth and FP32 pair-kernel tile length (blocks of 32)."""
+        """Current sort-key Hilbert depth and FP32 pair-kernel tile length (blocks of 32)."""
         b, t = ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.p3m_get_tuning(self._ctx, ctypes.byref(b), ctypes.byref(t)))
         return {"sub_bits": b.value, "tile_blocks": t.value}
 
     def autotune(self):
-        """Picks the sort key's Morton depth, then the FP32 pair kernel's tile length, by timing
+        """Picks the sort key's Hilbert depth, then the FP32 pair kernel's tile length, by timing
         force evaluations; returns (sub_bits, ms per evaluation for sub_bits 0..3)."""
         b = ctypes.c_int()
         ms = np.full(4, np.nan)

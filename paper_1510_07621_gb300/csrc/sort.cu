@@ -5,7 +5,10 @@
 // sets the cell size, Ch. Parameters "P3M_cutoff"): with n_f = n_c 2^b fine cells per side,
 //   f_d = min(trunc(x_d * (n_f / L)), n_f - 1)   (one correctly rounded FP64 multiply)
 //   cell = (c_z n_c + c_y) n_c + c_x,  c_d = f_d >> b
-//   key  = (cell << 3b) | Morton(f_x mod 2^b, f_y mod 2^b, f_z mod 2^b)
+//   key  = (cell << 3b) | Hilbert(f_x mod 2^b, f_y mod 2^b, f_z mod 2^b)
+// (Hilbert: the index along the 3-D Hilbert curve of order b, after Skilling, "Programming the
+// Hilbert curve", AIP Conf. Proc. 707, 2004; consecutive indices are face neighbours, so runs of
+// consecutive particles are more compact than along a Morton order)
 // Particles are ordered by key, ties by their current slot (a stable sort), so the order is
 // reproducible bit for bit.
 #include <cuda_runtime.h>
@@ -66,10 +69,30 @@ __device__ __forceinline__ uint32_t make_key(uint32_t fx, uint32_t fy, uint32_t 
     const int b = g.sub_bits;
     const uint32_t cell = ((fz >> b) * (uint32_t)g.n_c + (fy >> b)) * (uint32_t)g.n_c + (fx >> b);
     const uint32_t m = (1u << b) - 1u;
-    uint32_t sx = fx & m, sy = fy & m, sz = fz & m, code = 0;
-    for (int t = 0; t < b; ++t)
-        code |= (((sx >> t) & 1u) << (3 * t)) | (((sy >> t) & 1u) << (3 * t + 1)) |
-                (((sz >> t) & 1u) << (3 * t + 2));
+    uint32_t x[3] = {fx & m, fy & m, fz & m}, code = 0;
+    if (b > 0) {
+        const uint32_t top = 1u << (b - 1);
+        for (uint32_t q = top; q > 1; q >>= 1) {  // undo the excess rotations and reflections
+            const uint32_t low = q - 1;
+            for (int i = 0; i < 3; ++i) {
+                if (x[i] & q) {
+                    x[0] ^= low;
+                } else {
+                    const uint32_t t = (x[0] ^ x[i]) & low;
+                    x[0] ^= t;
+                    x[i] ^= t;
+                }
+            }
+        }
+        x[1] ^= x[0];  // Gray encode
+        x[2] ^= x[1];
+        uint32_t t = 0;
+        for (uint32_t q = top; q > 1; q >>= 1)
+            if (x[2] & q) t ^= q - 1;
+        for (int i = 0; i < 3; ++i) x[i] ^= t;
+        for (int level = b - 1; level >= 0; --level)
+            for (int i = 0; i < 3; ++i) code = (code << 1) | ((x[i] >> level) & 1u);
+    }
     return (cell << (3 * b)) | code;
 }
 

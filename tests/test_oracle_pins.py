@@ -248,12 +248,28 @@ def test_keys_brute_force():
         f = [min(int(pos[d, i] * p.n_fine / L), p.n_fine - 1) for d in range(3)]
         c = [fd >> 2 for fd in f]
         s = [fd & 3 for fd in f]
-        code = 0
-        for t in range(2):
-            for d in range(3):
-                code |= ((s[d] >> t) & 1) << (3 * t + d)
         assert cell[i] == (c[2] * 11 + c[1]) * 11 + c[0]
-        assert key[i] == (cell[i] << 6) | code
+        assert key[i] >> 6 == cell[i]
+        assert key[i] & 63 == O.hilbert3(np.array(s[0]), np.array(s[1]), np.array(s[2]), 2)
+
+
+@pytest.mark.parametrize("bits", [1, 2, 3, 4])
+def test_hilbert_index_is_a_nested_face_neighbour_walk(bits):
+    """The sub-cell order: a bijection of the 8^bits points onto 0..8^bits-1 that starts at the
+    origin, steps to a face neighbour every time (the Hilbert curve's locality), and visits
+    every aligned sub-cube of side 2^k in one contiguous run of indices (its nesting)."""
+    m = 1 << bits
+    g = np.indices((m, m, m)).reshape(3, -1)
+    h = O.hilbert3(g[0], g[1], g[2], bits)
+    assert np.array_equal(np.sort(h), np.arange(m ** 3))
+    walk = g[:, np.argsort(h)]
+    assert np.all(walk[:, 0] == 0)
+    assert np.all(np.abs(np.diff(walk, axis=1)).sum(0) == 1)
+    for k in range(1, bits):
+        side = 1 << k
+        cube = ((walk[0] // side) * m + walk[1] // side) * m + walk[2] // side
+        runs = np.count_nonzero(np.diff(cube)) + 1
+        assert runs == (m // side) ** 3  # each sub-cube entered once
 
 
 def test_stable_order_and_cell_start_brute_force():
