@@ -30,7 +30,10 @@ Readings where the guide is silent:
     taken at the unsoftened r;
   * units: H0 = 1 (time unit 1/H0), 4 pi G rho_bar = (3/2) Omega_m H0^2, so the per-particle
     coupling Gm = 3 Omega_m L^3 / (8 pi N);
-  * momentum p = m a^2 dx/dt; kick dp = m a_grav * int dt/a, drift dx = p/m * int dt/a^2.
+  * momentum p = m a^2 dx/dt; kick dp = m a_grav * int dt/a, drift dx = p/m * int dt/a^2;
+  * inside a chaining cell the particles are ordered by the 3-D Hilbert index of their fine
+    sub-cell (Skilling 2004), ties by input order: the guide fixes no order, the GPU path's
+    sort reproduces this one bit for bit.
 
 Arrays: positions/momenta/accelerations are float64 SoA of shape (3, N).
 """
