@@ -160,10 +160,9 @@ def oracle_step_time(pos, mom, n_sample, seed, with_pair=False):
 
 
 def oracle_pair_time_one_core(x, n_sample, seed):
-    """Seconds one host core needs for the oracle's pair sum of all particles of the wrapped
-    positions x, estimated from n_sample of them as in oracle_step_time (a child process with
-    OMP_NUM_THREADS=1).  Returns (seconds, particles sampled) or (None, 0) if the child
-    failed."""
+    """The oracle's pair sum of n_sample sampled particles of the wrapped positions x on one
+    host core (a child process with OMP_NUM_THREADS=1): returns (set-up seconds, seconds of the
+    per-target work, particles sampled), or (None, None, 0) if the child failed."""
     import subprocess
     import tempfile
     w = WORKLOAD
@@ -182,14 +181,14 @@ def oracle_pair_time_one_core(x, n_sample, seed):
             "t0 = time.perf_counter(); O.sr_accel(x, p, targets=tg[:1])\n"
             "t1 = time.perf_counter(); O.sr_accel(x, p, targets=tg)\n"
             "t2 = time.perf_counter(); su = t1 - t0\n"
-            "print(su + max(0.0, (t2 - t1) - su) * n / tg.size, tg.size, O.oracle_threads())\n")
+            "print(su, max(0.0, (t2 - t1) - su), tg.size, O.oracle_threads())\n")
         env = dict(os.environ, OMP_NUM_THREADS="1")
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                            timeout=600)
         if r.returncode != 0:
-            return None, 0
-        sec, size, threads = r.stdout.split()[-3:]
-        return (float(sec), int(size)) if int(threads) == 1 else (None, 0)
+            return None, None, 0
+        setup, work, size, threads = r.stdout.split()[-4:]
+        return (float(setup), float(work), int(size)) if int(threads) == 1 else (None, None, 0)
 
 
 # ---------------------------------------------------------------- replicas across ranks
@@ -415,13 +414,25 @@ def run_ours(args, rank, world, local_rank, dist):
         # the same step with the pair sum on one core (mesh part and kick/drift as measured)
         from oracle import p3m_oracle as O
         xw = O.wrap(snap_pos, w["box"])
-        pair_one, size1 = oracle_pair_time_one_core(xw, max(500, args.cpu_sample // 16), 98)
+        n1 = max(2000, args.cpu_sample // 4)
+        setup1, work1, size1 = oracle_pair_time_one_core(xw, n1, 98)
         one_core = None
-        if pair_one:
+        if work1:
+            # the same targets on all cores: the one-core factor of the per-target work
+            pp = O.Params(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"], w["softening"])
+            tg1 = np.unique((S.uniform01(98, n1) * n).astype(np.int64) % n)
+            t0 = time.perf_counter()
+            O.sr_accel(xw, pp, targets=tg1[:1])
+            t1 = time.perf_counter()
+            O.sr_accel(xw, pp, targets=tg1)
+            t2 = time.perf_counter()
+            setup_m, work_m = t1 - t0, max(1e-9, (t2 - t1) - (t1 - t0))
+            pair_one = setup1 + (pair_many - setup_m) * work1 / work_m
             sec_one = sec - pair_many + pair_one
             one_core = {"value": n / sec_one, "unit": UNIT, "cores": 1,
-                        "sample": f"pair sum estimated from {size1} sampled particles on one "
-                                  "core (set-up counted once); mesh force and kick/drift as in "
+                        "sample": f"the multi-core pair-sum estimate times the one-core factor "
+                                  f"{work1 / work_m:.1f} of the per-target work, measured on "
+                                  f"{size1} sampled particles; mesh force and kick/drift as in "
                                   "the multi-core figure"}
         out["cpu_baseline"] = {"value": n / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "one_core": one_core,
