@@ -64,14 +64,52 @@ __global__ void k_to_slots(const double *__restrict__ v, const uint32_t *__restr
     }
 }
 
-// u_b(node) += W(x_k - node) v_k,b, three meshes of type T.
-template <typename T>
+// The vector deposit u_b(node) = sum_k W(x_k - node) v_k,b accumulates in signed 64-bit fixed
+// point, like the mass deposit, so that its result does not depend on the order of the atomic
+// additions.  The scale 2^S comes from the largest |v|: with |v| < 2^e and N < 2^nb, every
+// partial sum stays below 2^61 in magnitude for S = 61 - nb - e.
+
+// *out = max |v| over n values, as the bit pattern of a non-negative double (those order like
+// unsigned integers, so the maximum does not depend on the order of the atomics either).
+__global__ void k_absmax_bits(const double *__restrict__ v, int64_t n, unsigned long long *__restrict__ out)
+{
+    unsigned long long m = 0ull;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v[k]));
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+        m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// s_out[0] = S for the largest |v| in *maxbits (0 when v is all zero or not finite).
+__global__ void k_fix_exponent(const unsigned long long *__restrict__ maxbits, int nb, int *__restrict__ s_out)
+{
+    const double m = __longlong_as_double((long long)*maxbits);
+    int S = 0;
+    if (m > 0.0 && m <= 1.7976931348623157e308) {
+        int e = 0;
+        frexp(m, &e);  // m < 2^e
+        S = 61 - nb - e;
+        S = S > 1000 ? 1000 : S;
+    }
+    s_out[0] = S;
+}
+
+// u_b(node) += W(x_k - node) v_k,b as round(W v 2^S) on three fixed-point meshes.
 __global__ void k_deposit_vec(const double *__restrict__ pos, const double *__restrict__ v,
-                              P3MGeom g, T *__restrict__ u)
+                              P3MGeom g, const int *__restrict__ s_dev,
+                              unsigned long long *__restrict__ fix)
 {
     const int M = g.mesh;
     const int64_t n = g.n;
     const size_t M3 = (size_t)M * M * M;
+    const double scale = ldexp(1.0, *s_dev);
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         int ix, iy, iz;
@@ -80,7 +118,7 @@ __global__ void k_deposit_vec(const double *__restrict__ pos, const double *__re
         stencil64(pos[n + k], g.inv_h, iy, fy);
         stencil64(pos[2 * n + k], g.inv_h, iz, fz);
         const double wx[2] = {1.0 - fx, fx}, wy[2] = {1.0 - fy, fy}, wz[2] = {1.0 - fz, fz};
-        const double vb[3] = {v[k], v[n + k], v[2 * n + k]};
+        const double vb[3] = {v[k] * scale, v[n + k] * scale, v[2 * n + k] * scale};
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -91,8 +129,23 @@ __global__ void k_deposit_vec(const double *__restrict__ pos, const double *__re
                     const size_t node = ((size_t)wrap_index(ix + a, M) * M + wrap_index(iy + b, M)) * M +
                                         wrap_index(iz + c, M);
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) atomicAdd(u + d * M3 + node, (T)(w * vb[d]));
+                    for (int d = 0; d < 3; ++d)
+                        atomicAdd(fix + d * M3 + node, (unsigned long long)__double2ll_rn(w * vb[d]));
                 }
+    }
+}
+
+// u = fix 2^-S (signed), and fix = 0 for the next deposit.
+template <typename T>
+__global__ void k_fix_to_vec(unsigned long long *__restrict__ fix, size_t n, const int *__restrict__ s_dev,
+                             T *__restrict__ u)
+{
+    const double inv_scale = ldexp(1.0, -*s_dev);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const long long v = (long long)fix[i];
+        fix[i] = 0ull;
+        u[i] = (T)(__ll2double_rn(v) * inv_scale);
     }
 }
 
@@ -859,10 +912,18 @@ cudaError_t vjp_mesh(p3m_ctx *c, const double *v_slots, double *out_slots)
     const int M = c->g.mesh;
     const size_t M3 = (size_t)M * M * M, nk = (size_t)M * M * (M / 2 + 1);
     T *u = (T *)c->adj_u;
-    cudaError_t e = cudaMemsetAsync(u, 0, 3 * M3 * sizeof(T), c->stream);
+    unsigned long long *maxbits = (unsigned long long *)(c->fix_exp + 2);
+    cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
-    c->launches += 3;
-    k_deposit_vec<T><<<grid_for(c->g.n, 256, c->num_sms), 256, 0, c->stream>>>(c->pos, v_slots, c->g, u);
+    int nb = 0;
+    while (nb < 63 && (c->g.n >> nb)) ++nb;
+    const int gn = grid_for(c->g.n, 256, c->num_sms);
+    c->launches += 6;
+    k_absmax_bits<<<gn, 256, 0, c->stream>>>(v_slots, 3 * c->g.n, maxbits);
+    k_fix_exponent<<<1, 1, 0, c->stream>>>(maxbits, nb, c->fix_exp);
+    k_deposit_vec<<<gn, 256, 0, c->stream>>>(c->pos, v_slots, c->g, c->fix_exp, c->rho_fix);
+    k_fix_to_vec<T><<<grid_for((int64_t)(3 * M3), 256, c->num_sms), 256, 0, c->stream>>>(c->rho_fix, 3 * M3,
+                                                                                       c->fix_exp, u);
     C2 *uk = (C2 *)c->frc_k;
     for (int b = 0; b < 3; ++b) {
         cufftResult r = sizeof(T) == 4

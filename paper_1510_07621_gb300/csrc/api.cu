@@ -185,7 +185,8 @@ void release(p3m_ctx *c)
                     c->tab_one,   c->ps_acc,   c->fac_table,    c->step_idx, c->cur_fac,
                     c->tab_origin,
                     c->adj_u,     c->adj_vfx,  c->adj_vs,       c->adj_out,  c->kself,
-                    c->li,        c->relx,     c->sort_status,  c->sort_hist};
+                    c->li,        c->relx,     c->sort_status,  c->sort_hist,
+                    c->rho_fix,   c->fix_exp,  c->ps_part};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -530,6 +531,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->tab_k, real * M},   {(void **)&c->tab_kg, real * M},
             {(void **)&c->tab_g, real * M},   {(void **)&c->tab_invw2, 8 * M},
             {(void **)&c->tab_one, 8 * M},    {(void **)&c->ps_acc, 8 * (3 * (M / 2) + 1)},
+            {(void **)&c->ps_part, 8 * (3 * (M / 2) + 1) * (size_t)(2 * c->num_sms)},
+            {(void **)&c->rho_fix, 8 * 3 * M3}, {(void **)&c->fix_exp, 16},
             {(void **)&c->tab_origin, 8 * (size_t)g.n_c},
             {(void **)&c->fac_table, 8 * 4 * (size_t)P3M_MAX_GRAPH_STEPS},
             {(void **)&c->step_idx, 16},      {(void **)&c->cur_fac, 32},
@@ -548,6 +551,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         if (rc != P3M_OK) break;
         cudaMemsetAsync(c->counters, 0, 16, c->stream);
         cudaMemsetAsync(c->pair_count, 0, 64, c->stream);
+        cudaMemsetAsync(c->rho_fix, 0, 8 * 3 * M3, c->stream);
+        c->ps_blocks = 2 * c->num_sms;
         if (opt.precision == P3M_PREC_MIXED)  // padding past the last particle stays zero
             cudaMemsetAsync(c->adj_vfx, 0, 384 * ((N + 31) / 32), c->stream);
 

@@ -14,14 +14,6 @@
 
 namespace {
 
-template <typename T>
-__global__ void k_fill(T *__restrict__ a, size_t n, T v)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        a[i] = v;
-}
-
 __device__ __forceinline__ int wrap_index(int i, int M)
 {
     i %= M;
@@ -61,6 +53,24 @@ __device__ __forceinline__ void cic_stencil_rel(const float4 rv, uint32_t cell, 
     }
 }
 
+// Fixed-point mass: every CIC weight (or run sum of weights) is rounded once to an integer
+// multiple of 2^-S and added as a 64-bit integer.  Integer addition is associative, so the
+// mesh does not depend on the order in which the atomics land: two runs give the same bits.
+// FP32 mode: S = 32 (weights are FP32 values, so 2^-33 is below their own rounding); FP64
+// mode: S = 62 - bit length of N, the finest scale at which N unit masses on one node still fit.
+template <typename T>
+__device__ __forceinline__ unsigned long long to_fixed(T w, T scale);
+template <>
+__device__ __forceinline__ unsigned long long to_fixed<float>(float w, float scale)
+{
+    return __float2ull_rn(w * scale);
+}
+template <>
+__device__ __forceinline__ unsigned long long to_fixed<double>(double w, double scale)
+{
+    return __double2ull_rn(w * scale);
+}
+
 // Fixed-size chunks of the sorted particles (CTA b takes slots [b*512, (b+1)*512)), so that a
 // dense cell is spread over many CTAs.  The chunk's CIC nodes are accumulated in a shared-memory
 // tile spanning the chunk's node bounding box (found by a block reduction); the tile is then
@@ -68,19 +78,21 @@ __device__ __forceinline__ void cic_stencil_rel(const float4 rv, uint32_t cell, 
 // particles than box nodes); a sparse chunk, whose box holds more nodes than it has particles,
 // adds its 8 weights per particle straight to the mesh (measured: 10-18 % faster deposits on
 // clustered and near-uniform states than tiles for every chunk), as does a chunk whose box
-// exceeds the tile capacity (e.g. one that straddles the periodic boundary).
+// exceeds the tile capacity (e.g. one that straddles the periodic boundary).  All sums are
+// 64-bit fixed-point integers (to_fixed).
 constexpr int kDepChunk = 512;
 constexpr int kDepTileMax = 4096;  // nodes
 
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_deposit_chunks(const double *__restrict__ pos, const float4 *__restrict__ rel,
-                     const uint32_t *__restrict__ keys, P3MGeom g, T *__restrict__ mesh)
+                     const uint32_t *__restrict__ keys, P3MGeom g, T scale,
+                     unsigned long long *__restrict__ fix)
 {
     // rel != nullptr (FP32 mode, sorted state fresh): FP32 stencils from rel and the keys' cells
     const float inv_h_f = (float)g.inv_h, inv_nc = 1.0f / (float)g.n_c;
     const int csh = 3 * g.sub_bits;
-    __shared__ T tile[kDepTileMax];
+    __shared__ unsigned long long tile[kDepTileMax];
     __shared__ int s_lo[3][8], s_hi[3][8];
     const int M = g.mesh;
     const int64_t n = g.n;
@@ -143,7 +155,7 @@ __global__ void __launch_bounds__(256)
     }
     const long long vol = (long long)bdim[0] * bdim[1] * bdim[2];
     if (vol <= kDepTileMax && vol <= kDepChunk) {
-        for (int t = threadIdx.x; t < vol; t += 256) tile[t] = T(0);
+        for (int t = threadIdx.x; t < vol; t += 256) tile[t] = 0ull;
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < per; ++r) {
@@ -160,7 +172,8 @@ __global__ void __launch_bounds__(256)
             for (int c = 0; c < 8; ++c) w[c] = wx[c >> 2] * wy[(c >> 1) & 1] * wz[c & 1];
             if (__popc(heads) <= 8) {
                 // few runs (dense region): each run's weights summed onto its first lane by a
-                // segmented reduction, then one set of 8 shared-memory atomics per run
+                // segmented reduction (a fixed order of additions for a given particle order),
+                // then one set of 8 shared-memory atomics per run
                 const int rid = __popc(heads & ((2u << lane) - 1u));
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
@@ -180,19 +193,19 @@ __global__ void __launch_bounds__(256)
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    T *row = tile + ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
-                    atomicAdd(row, w[(a << 2) | (b << 1)]);
-                    atomicAdd(row + 1, w[(a << 2) | (b << 1) | 1]);
+                    unsigned long long *row = tile + ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
+                    atomicAdd(row, to_fixed(w[(a << 2) | (b << 1)], scale));
+                    atomicAdd(row + 1, to_fixed(w[(a << 2) | (b << 1) | 1], scale));
                 }
         }
         __syncthreads();
         for (int t = threadIdx.x; t < vol; t += 256) {
-            const T v = tile[t];
-            if (v != T(0)) {
+            const unsigned long long v = tile[t];
+            if (v != 0ull) {
                 const int lz = t % bdim[2], ly = (t / bdim[2]) % bdim[1], lx = t / (bdim[2] * bdim[1]);
                 const size_t node = ((size_t)wrap_index(blo[0] + lx, M) * M + wrap_index(blo[1] + ly, M)) * M +
                                     wrap_index(blo[2] + lz, M);
-                atomicAdd(mesh + node, v);
+                atomicAdd(fix + node, v);
             }
         }
     } else {
@@ -209,9 +222,37 @@ __global__ void __launch_bounds__(256)
                     for (int c = 0; c < 2; ++c) {
                         const size_t node = ((size_t)wrap_index(i0[r][0] + a, M) * M +
                                              wrap_index(i0[r][1] + b, M)) * M + wrap_index(i0[r][2] + c, M);
-                        atomicAdd(mesh + node, wx[a] * wy[b] * wz[c]);
+                        atomicAdd(fix + node, to_fixed(wx[a] * wy[b] * wz[c], scale));
                     }
         }
+    }
+}
+
+// mesh = fix 2^-S - mean, and fix = 0 for the next deposit.  FP32 mode (S = 32): the high and
+// low 32-bit words convert exactly or with one rounding each, (hi - mean) + lo 2^-32 rounds
+// twice, so the result is within about one FP32 unit of the exact value.  FP64 mode: one
+// conversion and one FMA.
+__global__ void __launch_bounds__(256)
+    k_fix_to_mesh_f32(unsigned long long *__restrict__ fix, size_t n, float mean, float *__restrict__ mesh)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = fix[i];
+        fix[i] = 0ull;
+        const float hi = __uint2float_rn((uint32_t)(v >> 32)), lo = __uint2float_rn((uint32_t)v);
+        mesh[i] = fmaf(lo, 0x1p-32f, hi - mean);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_fix_to_mesh_f64(unsigned long long *__restrict__ fix, size_t n, double inv_scale, double mean,
+                      double *__restrict__ mesh)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = fix[i];
+        fix[i] = 0ull;
+        mesh[i] = fma(__ull2double_rn(v), inv_scale, -mean);
     }
 }
 
@@ -304,45 +345,88 @@ __global__ void __launch_bounds__(256)
 // delta_k = rho_k / N; every mode (ix, iy, iz) stands for itself and, for 0 < iz < M/2, for its
 // conjugate partner (weight 2).  Shell b = round(|n|) - 1 accumulates w |delta_k|^2 / W^2,
 // w |k| and w; with radius > 0 the top-hat sum w |delta_k|^2 / W^2 W_TH(|k| R)^2 goes to
-// acc[3 n_bins].  Per-block shared-memory partial sums, then one FP64 atomic per bin.
+// row entry 3 n_bins.  The additions happen in an order fixed by the launch shape alone: the
+// lanes of a warp that hold modes of one shell are summed in lane order by the lowest of them,
+// which adds the sums to its warp's private shared-memory row; the block adds its warps' rows in
+// warp order into its row of part[], and k_powspec_final adds the blocks' rows in block order.
+// So every run gives the same bits.
 template <typename C2>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
     k_powspec(const C2 *__restrict__ rk, int M, const double *__restrict__ inv_w2, double kf,
-              double inv_n2, double radius, int n_bins, double *__restrict__ acc)
+              double inv_n2, double radius, int n_bins, double *__restrict__ part)
 {
-    extern __shared__ double sacc[];  // 3 * n_bins + 1
+    extern __shared__ double sacc[];  // (blockDim / 32) rows of 3 n_bins + 1
     const int nacc = 3 * n_bins + 1;
-    for (int t = threadIdx.x; t < nacc; t += blockDim.x) sacc[t] = 0.0;
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double *mine = sacc + (size_t)warp * nacc;
+    for (int t = lane; t < nacc; t += 32) mine[t] = 0.0;
+    __syncwarp();
     const int nz = M / 2 + 1;
     const size_t total = (size_t)M * M * nz;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        if (idx == 0) continue;
-        const int iz = (int)(idx % nz);
-        const size_t t = idx / nz;
-        const int iy = (int)(t % M), ix = (int)(t / M);
-        const int sx = ix <= M / 2 ? ix : ix - M, sy = iy <= M / 2 ? iy : iy - M;
-        const double w = (iz == 0 || iz == M / 2) ? 1.0 : 2.0;
-        const double nk = sqrt((double)sx * sx + (double)sy * sy + (double)iz * iz);
-        const C2 r = rk[idx];
-        const double p = ((double)r.x * r.x + (double)r.y * r.y) * inv_n2 * inv_w2[ix] * inv_w2[iy] *
-                         inv_w2[iz];
-        const int b = (int)floor(nk + 0.5) - 1;
-        if (b < n_bins) {
-            atomicAdd(&sacc[3 * b], w * p);
-            atomicAdd(&sacc[3 * b + 1], w * nk * kf);
-            atomicAdd(&sacc[3 * b + 2], w);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = ((size_t)blockIdx.x * nw + warp) * 32; base < total; base += stride) {
+        const size_t idx = base + lane;
+        int b = -1;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, vt = 0.0;
+        if (idx < total && idx != 0) {
+            const int iz = (int)(idx % nz);
+            const size_t t = idx / nz;
+            const int iy = (int)(t % M), ix = (int)(t / M);
+            const int sx = ix <= M / 2 ? ix : ix - M, sy = iy <= M / 2 ? iy : iy - M;
+            const double w = (iz == 0 || iz == M / 2) ? 1.0 : 2.0;
+            const double nk = sqrt((double)sx * sx + (double)sy * sy + (double)iz * iz);
+            const C2 r = rk[idx];
+            const double p = ((double)r.x * r.x + (double)r.y * r.y) * inv_n2 * inv_w2[ix] *
+                             inv_w2[iy] * inv_w2[iz];
+            b = (int)floor(nk + 0.5) - 1;
+            if (b >= n_bins) b = -1;
+            v0 = w * p;
+            v1 = w * nk * kf;
+            v2 = w;
+            if (radius > 0.0) {
+                const double x = nk * kf * radius;
+                const double wt = x < 1e-3 ? 1.0 - x * x / 10.0 : 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
+                vt = w * p * wt * wt;
+            }
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, b);
+        if (b >= 0) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (unsigned m = grp; m; m &= m - 1u) {
+                const int src = __ffs(m) - 1;
+                s0 += __shfl_sync(grp, v0, src);
+                s1 += __shfl_sync(grp, v1, src);
+                s2 += __shfl_sync(grp, v2, src);
+            }
+            if (lane == __ffs(grp) - 1) {
+                mine[3 * b] += s0;
+                mine[3 * b + 1] += s1;
+                mine[3 * b + 2] += s2;
+            }
         }
         if (radius > 0.0) {
-            const double x = nk * kf * radius;
-            const double wt = x < 1e-3 ? 1.0 - x * x / 10.0 : 3.0 * (sin(x) - x * cos(x)) / (x * x * x);
-            atomicAdd(&sacc[3 * n_bins], w * p * wt * wt);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vt += __shfl_xor_sync(0xffffffffu, vt, o);
+            if (lane == 0) mine[3 * n_bins] += vt;
         }
+        __syncwarp();
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nacc; t += blockDim.x)
-        if (sacc[t] != 0.0) atomicAdd(&acc[t], sacc[t]);
+    for (int t = threadIdx.x; t < nacc; t += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sacc[(size_t)w * nacc + t];
+        part[(size_t)blockIdx.x * nacc + t] = s;
+    }
+}
+
+__global__ void k_powspec_final(const double *__restrict__ part, int blocks, int nacc,
+                                double *__restrict__ acc)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nacc; t += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < blocks; ++b) s += part[(size_t)b * nacc + t];
+        acc[t] = s;
+    }
 }
 
 inline int grid_for(size_t n, int threads, int num_sms)
@@ -353,17 +437,32 @@ inline int grid_for(size_t n, int threads, int num_sms)
     return (int)(b < 1 ? 1 : b);
 }
 
+// Bit length of n (the S of the FP64 mode's fixed point is 62 minus it).
+int bit_length(int64_t n)
+{
+    int b = 0;
+    while (b < 63 && (n >> b)) ++b;
+    return b;
+}
+
 template <typename T>
 cudaError_t deposit_impl(p3m_ctx *c, bool from_rel)
 {
     const size_t M3 = (size_t)c->g.mesh * c->g.mesh * c->g.mesh;
-    T *mesh = (T *)c->rho;
-    c->launches += 2;  // fill, deposit
-    k_fill<T><<<grid_for(M3, 256, c->num_sms), 256, 0, c->stream>>>(mesh, M3, (T)(-c->g.mean_count));
+    const bool f32 = sizeof(T) == 4;
+    const int S = f32 ? 32 : 62 - bit_length(c->g.n);
+    c->launches += 2;  // deposit, conversion
     const int64_t chunks = (c->g.n + kDepChunk - 1) / kDepChunk;
     k_deposit_chunks<T><<<(unsigned)chunks, 256, 0, c->stream>>>(
         c->pos, from_rel && c->precision == P3M_PREC_MIXED ? (const float4 *)c->rel : nullptr,
-        c->keys, c->g, mesh);
+        c->keys, c->g, (T)ldexp(1.0, S), c->rho_fix);
+    const int grid = grid_for(M3, 256, c->num_sms);
+    if (f32)
+        k_fix_to_mesh_f32<<<grid, 256, 0, c->stream>>>(c->rho_fix, M3, (float)c->g.mean_count,
+                                                       (float *)c->rho);
+    else
+        k_fix_to_mesh_f64<<<grid, 256, 0, c->stream>>>(c->rho_fix, M3, ldexp(1.0, -S), c->g.mean_count,
+                                                       (double *)c->rho);
     return cudaGetLastError();
 }
 
@@ -398,18 +497,28 @@ cudaError_t launch_kspace(p3m_ctx *c)
 cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc)
 {
     const int M = c->g.mesh;
-    const size_t smem = sizeof(double) * (3 * (size_t)n_bins + 1);
-    const int grid = c->num_sms * 4;
+    const int nacc = 3 * n_bins + 1, threads = 128;
+    const size_t smem = sizeof(double) * (size_t)nacc * (threads / 32);
     const double kf = 2.0 * M_PI / c->g.box;
     const double inv_n2 = 1.0 / ((double)c->g.n * (double)c->g.n);
-    c->launches += 1;
-    cudaMemsetAsync(acc, 0, smem, c->stream);
-    if (c->precision == P3M_PREC_MIXED)
-        k_powspec<cufftComplex><<<grid, 256, smem, c->stream>>>((const cufftComplex *)c->rho_k, M, inv_w2,
-                                                               kf, inv_n2, radius, n_bins, acc);
-    else
-        k_powspec<cufftDoubleComplex><<<grid, 256, smem, c->stream>>>(
-            (const cufftDoubleComplex *)c->rho_k, M, inv_w2, kf, inv_n2, radius, n_bins, acc);
+    c->launches += 2;
+    cudaError_t e = cudaSuccess;
+    if (c->precision == P3M_PREC_MIXED) {
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(k_powspec<cufftComplex>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e != cudaSuccess) return e;
+        k_powspec<cufftComplex><<<c->ps_blocks, threads, smem, c->stream>>>(
+            (const cufftComplex *)c->rho_k, M, inv_w2, kf, inv_n2, radius, n_bins, c->ps_part);
+    } else {
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(k_powspec<cufftDoubleComplex>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_powspec<cufftDoubleComplex><<<c->ps_blocks, threads, smem, c->stream>>>(
+            (const cufftDoubleComplex *)c->rho_k, M, inv_w2, kf, inv_n2, radius, n_bins, c->ps_part);
+    }
+    k_powspec_final<<<(nacc + 255) / 256, 256, 0, c->stream>>>(c->ps_part, c->ps_blocks, nacc, acc);
     return cudaGetLastError();
 }
 

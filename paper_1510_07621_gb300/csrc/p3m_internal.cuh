@@ -81,7 +81,14 @@ struct p3m_ctx {
     double *tab_invw2;             // per-axis 1/sinc^4(k h/2) (FP64, length M)
     double *tab_one;               // M ones (no deconvolution)
     double *tab_origin;            // n_c chaining-cell origins c * cs (FP64, correctly rounded)
-    double *ps_acc;                // power spectrum partial sums (3 * (M/2) + 1)
+    double *ps_acc;                // power spectrum sums (3 * (M/2) + 1)
+    double *ps_part;               // power spectrum per-block partial sums (ps_blocks rows)
+    int ps_blocks;
+    // fixed-point deposit accumulator: 3 M^3 64-bit integers, all zero between deposits (each
+    // conversion pass clears what it read); sums of integers do not depend on the order of the
+    // atomic additions, so every run gives the same mesh
+    unsigned long long *rho_fix;
+    int *fix_exp;  // scale exponent of the vector deposit (set on the device)
     double green_const;
     float gpoly[12];  // FP32 split factor: g = 1 + r^3 Q(tau), Q = sum gpoly[k] tau^k
                       // (k <= P3M_SPLIT_DEG), tau = r^2 gpoly[11] - 1
