@@ -125,12 +125,26 @@ class ClockSampler:
 # ---------------------------------------------------------------- oracle timing (host)
 
 
-def oracle_step_time(pos, mom, n_sample, seed, with_pair=False):
-    """Seconds the FP64 oracle needs for one step of this particle set: the full mesh force
-    (all particles), the pair sum of all particles estimated from n_sample of them, and the
-    kick/drift of all particles.  The pair sum's set-up (cell keys, order and ranges of all N
-    particles, timed by a call with one target) is counted once; only the per-target part is
-    scaled by N / n_sample.  Returns (seconds, threads, description[, pair-sum seconds])."""
+def stratified_targets(x, stride, offset=0):
+    """Every stride-th particle along the oracle's cell order (chaining cells, Hilbert order
+    inside them): a sample that holds dense and sparse regions in proportion, so that the
+    per-target cost of the pair sum, which grows with the local density, averages like the
+    whole set's."""
+    from oracle import p3m_oracle as O
+    w = WORKLOAD
+    q = O.Params(w["box"], x.shape[1], w["mesh"], w["r_s_cells"], w["cutoff"], w["softening"],
+                 sub_bits=3)
+    _, key = O.cell_keys(x, q)
+    return np.sort(O.stable_order(key)[offset::stride])
+
+
+def oracle_step(pos, mom, stride=1, offset=0):
+    """One step of the FP64 oracle on this particle set, timed on the host: the full mesh force
+    (all particles), the short-range pair sum, and the kick/drift of all particles.  stride = 1:
+    the pair sum of every particle.  stride > 1: the pair sum of the stratified sample of every
+    stride-th particle, its per-target time scaled by stride (the set-up of cell keys, order and
+    ranges of all N particles, timed by a call with one target, is counted once).  Returns a dict
+    of seconds per part, the threads the oracle used and accepted pairs per target particle."""
     from oracle import p3m_oracle as O
     w = WORKLOAD
     n = pos.shape[1]
@@ -139,56 +153,51 @@ def oracle_step_time(pos, mom, n_sample, seed, with_pair=False):
     t0 = time.perf_counter()
     lr = O.pm_accel(x, p)
     t1 = time.perf_counter()
-    tg = np.unique((S.uniform01(seed, n_sample) * n).astype(np.int64) % n)
-    O.sr_accel(x, p, targets=tg[:1])
-    t1b = time.perf_counter()
-    O.sr_accel(x, p, targets=tg)
-    t2 = time.perf_counter()
+    if stride > 1:
+        tg = stratified_targets(x, stride, offset)
+        t1 = time.perf_counter()
+        O.sr_accel(x, p, targets=tg[:1])
+        t1b = time.perf_counter()
+        _, npairs = O.sr_accel(x, p, targets=tg)
+        t2 = time.perf_counter()
+        setup = t1b - t1
+        pair = setup + max(0.0, (t2 - t1b) - setup) * (n / tg.size)
+        nt = tg.size
+    else:
+        _, npairs = O.sr_accel(x, p)
+        t2 = time.perf_counter()
+        pair = t2 - t1
+        nt = n
     m = mom + lr * O.kick_factor(1.0, 1.02, p)
     x2 = O.wrap(x + m * O.drift_factor(1.0, 1.04, p), w["box"])
     del x2
     t3 = time.perf_counter()
-    setup = t1b - t1
-    pair = setup + max(0.0, (t2 - t1b) - setup) * n / tg.size
-    total = (t1 - t0) + pair + (t3 - t2)
-    desc = (f"full mesh force and kick/drift for all {n} particles; short-range pair sum for "
-            f"{tg.size} sampled particles, its per-target time scaled by {n / tg.size:.1f} "
-            "(set-up counted once)")
-    if with_pair:
-        return total, O.oracle_threads(), desc, pair
-    return total, O.oracle_threads(), desc
+    return {"seconds": (t1 - t0) + pair + (t3 - t2), "mesh_s": t1 - t0, "pair_s": pair,
+            "kick_drift_s": t3 - t2, "threads": O.oracle_threads(), "targets": nt,
+            "pairs_per_particle": npairs / nt}
 
 
-def oracle_pair_time_one_core(x, n_sample, seed):
-    """The oracle's pair sum of n_sample sampled particles of the wrapped positions x on one
-    host core (a child process with OMP_NUM_THREADS=1): returns (set-up seconds, seconds of the
-    per-target work, particles sampled), or (None, None, 0) if the child failed."""
+def oracle_step_one_core(pos, mom, stride):
+    """oracle_step on one host core (a child process with OMP_NUM_THREADS=1; numpy's FFT and
+    array arithmetic are single-threaded): the dict of oracle_step, or None if the child failed."""
     import subprocess
     import tempfile
-    w = WORKLOAD
     with tempfile.TemporaryDirectory() as tmp:
-        path = os.path.join(tmp, "x.npy")
-        np.save(path, x)
+        px, pm = os.path.join(tmp, "x.npy"), os.path.join(tmp, "m.npy")
+        np.save(px, pos)
+        np.save(pm, mom)
         code = (
-            "import sys, time, numpy as np\n"
+            "import sys, json, numpy as np\n"
             f"sys.path.insert(0, {ROOT!r})\n"
-            "import p3m_synth as S\n"
-            "from oracle import p3m_oracle as O\n"
-            f"x = np.load({path!r}); n = x.shape[1]\n"
-            f"p = O.Params({w['box']!r}, n, {w['mesh']!r}, {w['r_s_cells']!r}, {w['cutoff']!r}, "
-            f"{w['softening']!r})\n"
-            f"tg = np.unique((S.uniform01({seed}, {n_sample}) * n).astype(np.int64) % n)\n"
-            "t0 = time.perf_counter(); O.sr_accel(x, p, targets=tg[:1])\n"
-            "t1 = time.perf_counter(); O.sr_accel(x, p, targets=tg)\n"
-            "t2 = time.perf_counter(); su = t1 - t0\n"
-            "print(su, max(0.0, (t2 - t1) - su), tg.size, O.oracle_threads())\n")
+            "import bench\n"
+            f"print(json.dumps(bench.oracle_step(np.load({px!r}), np.load({pm!r}), {stride})))\n")
         env = dict(os.environ, OMP_NUM_THREADS="1")
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                           timeout=600)
+                           timeout=900)
         if r.returncode != 0:
-            return None, None, 0
-        setup, work, size, threads = r.stdout.split()[-4:]
-        return (float(setup), float(work), int(size)) if int(threads) == 1 else (None, None, 0)
+            return None
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return d if d["threads"] == 1 else None
 
 
 # ---------------------------------------------------------------- replicas across ranks
@@ -406,39 +415,52 @@ def run_ours(args, rank, world, local_rank, dist):
                            "speedup_mixed_over_fp64": value / world / (n / (ms64 / 1e3))}
 
     # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1 only), on the
-    # synthetic clustered a = 1 stand-in snapshot: no oracle input comes from the GPU path
-    if rank == 0 and world == 1 and args.cpu_sample > 0:
+    # synthetic clustered a = 1 stand-in snapshot: no oracle input comes from the GPU path.  The
+    # GPU path is timed on the same snapshot too, so that the two rates compare like work.
+    if rank == 0 and world == 1 and args.cpu_stride > 0:
         snap_pos, snap_mom = S.clustered(w["n_p"], w["box"], w["seed"])
-        sec, threads, desc, pair_many = oracle_step_time(snap_pos, snap_mom, args.cpu_sample, 99,
-                                                         with_pair=True)
-        # the same step with the pair sum on one core (mesh part and kick/drift as measured)
-        from oracle import p3m_oracle as O
-        xw = O.wrap(snap_pos, w["box"])
-        n1 = max(2000, args.cpu_sample // 4)
-        setup1, work1, size1 = oracle_pair_time_one_core(xw, n1, 98)
-        one_core = None
-        if work1:
-            # the same targets on all cores: the one-core factor of the per-target work
-            pp = O.Params(w["box"], n, w["mesh"], w["r_s_cells"], w["cutoff"], w["softening"])
-            tg1 = np.unique((S.uniform01(98, n1) * n).astype(np.int64) % n)
-            t0 = time.perf_counter()
-            O.sr_accel(xw, pp, targets=tg1[:1])
-            t1 = time.perf_counter()
-            O.sr_accel(xw, pp, targets=tg1)
-            t2 = time.perf_counter()
-            setup_m, work_m = t1 - t0, max(1e-9, (t2 - t1) - (t1 - t0))
-            pair_one = setup1 + (pair_many - setup_m) * work1 / work_m
-            sec_one = sec - pair_many + pair_one
-            one_core = {"value": n / sec_one, "unit": UNIT, "cores": 1,
-                        "sample": f"the multi-core pair-sum estimate times the one-core factor "
-                                  f"{work1 / work_m:.1f} of the per-target work, measured on "
-                                  f"{size1} sampled particles; mesh force and kick/drift as in "
-                                  "the multi-core figure"}
-        out["cpu_baseline"] = {"value": n / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "one_core": one_core,
-                               "sample": desc + "; on the synthetic clustered a=1 stand-in "
-                                                "snapshot of the same size",
-                               "seconds_per_step_estimate": sec}
+        sim.set_particles(snap_pos, snap_mom, a=1.0)
+        sim.forces(1.0)
+        torch.cuda.synchronize(dev)
+        d0 = sim.diagnostics()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a_s = 1.0
+        for _ in range(5):
+            sim.step(a_s, MEASURE_DA * a_s)
+            a_s *= 1.0 + MEASURE_DA
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_si = e0.elapsed_time(e1) / 5
+        d1 = sim.diagnostics()
+        gpu_stand_in = {"value": n / (ms_si / 1e3), "unit": UNIT, "ms_per_step": ms_si, "steps": 5,
+                        "pairs_per_particle": (d1["pairs_total"] - d0["pairs_total"]) / 5 / n}
+        full = oracle_step(snap_pos, snap_mom, args.cpu_stride)
+        est = oracle_step(snap_pos, snap_mom, 64) if args.cpu_stride == 1 else None
+        one = oracle_step_one_core(snap_pos, snap_mom, 64)
+        what = ("all particles" if args.cpu_stride == 1 else
+                f"the stratified sample of every {args.cpu_stride}th particle in cell order, its "
+                "per-target time scaled")
+        out["cpu_baseline"] = {
+            "value": n / full["seconds"], "unit": UNIT, "cores": full["threads"], "kind": "oracle",
+            "sample": (f"one full oracle step of the synthetic clustered a=1 stand-in snapshot "
+                       f"({n} particles): mesh force and kick/drift of all particles, short-range "
+                       f"pair sum of {what}"),
+            "seconds_per_step": full["seconds"],
+            "parts_s": {k: full[k] for k in ("mesh_s", "pair_s", "kick_drift_s")},
+            "pairs_per_particle": {"stand_in": full["pairs_per_particle"],
+                                   "gpu_timed_state": pairs_per_step / n},
+            "gpu_on_stand_in": gpu_stand_in,
+            "stratified_estimate_64": None if est is None else {
+                "value": n / est["seconds"], "targets": est["targets"],
+                "pair_s": est["pair_s"]},
+            "one_core": None if one is None else {
+                "value": n / one["seconds"], "unit": UNIT, "cores": 1,
+                "seconds_per_step": one["seconds"],
+                "sample": "one oracle step in a one-thread child process: mesh force and "
+                          "kick/drift of all particles, pair sum of the stratified sample of "
+                          f"every 64th particle ({one['targets']} targets), its per-target time "
+                          "scaled by 64"}}
     sim.close()
     return out
 
@@ -604,28 +626,37 @@ def run_adjoint(args):
 
 
 def run_reference(args):
-    from oracle import p3m_oracle as O
+    """The oracle as the reference arm: K timed steps (after W untimed ones) on the synthetic
+    clustered a=1 stand-in snapshot, each one full oracle step except that the pair sum runs on
+    a stratified sample (every stride-th particle in cell order, stride = max(16, 4 K), its
+    per-target time scaled; a different offset each step), so that K + W steps end within a few
+    minutes.  The same estimator as the cpu_baseline of our arm."""
     w = WORKLOAD
     n = w["n_p"] ** 3
     pos, mom = S.clustered(w["n_p"], w["box"], w["seed"])
-    # the pair-sum sample of one step shrinks with the number of steps, so that the whole run
-    # (each step also computes the full mesh force, several seconds) ends within minutes
-    per_step = max(500, args.cpu_sample // max(1, args.steps))
-    for _ in range(args.warmup):
-        oracle_step_time(pos, mom, 500, 5)
-    total = 0.0
-    threads, desc = 1, ""
+    stride = args.ref_stride or max(16, 4 * args.steps)
+    for k in range(args.warmup):
+        oracle_step(pos, mom, stride, offset=(k + 1) % stride)
+    total, executed, threads, ppp = 0.0, 0, 1, 0.0
     for k in range(args.steps):
-        sec, threads, desc = oracle_step_time(pos, mom, per_step, 100 + k)
-        total += sec
-    value = n * args.steps / total
+        d = oracle_step(pos, mom, stride, offset=(k + args.warmup + 1) % stride)
+        total += d["seconds"]
+        threads = d["threads"]
+        ppp = d["pairs_per_particle"]
+        executed += 1
+    value = n * executed / total
+    desc = (f"{executed} oracle steps, each: mesh force and kick/drift of all {n} particles, "
+            f"pair sum of the stratified sample of every {stride}th particle in cell order, its "
+            "per-target time scaled")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "steps_executed": executed, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / executed,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME.split(";")[0] +
                        "; synthetic clustered a=1 stand-in snapshot (no GPU evolution)",
-                       "particles": n, "mesh": w["mesh"]},
+                       "particles": n, "mesh": w["mesh"], "pair_sample_stride": stride,
+                       "pairs_per_particle": ppp},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -698,6 +729,102 @@ def run_zeldovich512(args):
             "gpu_launches": int(d1["launches"] - d0["launches"])}
 
 
+# ---------------------------------------------------------------- the other configurations
+
+
+def other_configs(args):
+    """The 512^3 run, the 48-simulation ensemble and the differentiable run, each measured in
+    this process after the main workload (N = 1, rank 0): their key figures for the default
+    benchmark line."""
+    import torch
+    out = {}
+    z = run_zeldovich512(args)
+    out["zeldovich512"] = {k: z[k] for k in ("value", "unit", "ms_per_step", "force_evaluation_ms",
+                                             "roofline", "pairs_per_step", "gpu_launches")}
+    out["zeldovich512"]["workload"] = z["config"]["workload"]
+    out["zeldovich512"]["phase_ms_per_evaluation"] = {k: v / 11 for k, v in z["phase_ms_total"].items()}
+    torch.cuda.empty_cache()
+    e = run_ensemble(args)
+    out["ensemble48"] = {"value": e["value"], "unit": e["unit"], "workload": e["config"]["workload"],
+                         "modes": e["modes"],
+                         "speedup_graph_over_serial": e["speedup_graph_over_serial"]}
+    torch.cuda.empty_cache()
+    d = run_adjoint(args)
+    out["adjoint128"] = {k: d[k] for k in ("value", "unit", "forward_ms_per_step",
+                                           "adjoint_ms_per_step", "adjoint_over_forward", "loss")}
+    out["adjoint128"]["workload"] = d["config"]["workload"]
+    torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------- profiling cases
+
+
+PROFILE_CASES = ("evolved_128", "clustered_128", "uniform_128", "eds_32", "zeldovich_256",
+                 "zeldovich_512")
+
+
+def run_profile_case(args):
+    """One workload for a profiler (ncu): set-up, then ``--evals`` force evaluations (or steps
+    with ``--profile-steps``); prints the per-phase CUDA-event times of those evaluations.
+
+    evolved_128    128^3 Zel'dovich ICs (box 200, mesh 128) evolved 64 log steps a=0.02->1
+    clustered_128  the synthetic clustered 128^3 stand-in snapshot (no evolution)
+    uniform_128    128^3 Zel'dovich ICs at a = 0.02 (box 200, mesh 128): near-uniform cells
+    eds_32         32^3 Zel'dovich ICs at a = 0.02 (box 64, mesh 32)
+    zeldovich_256  256^3 Zel'dovich ICs at a = 0.5 (box 500, mesh 256): the 512^3 run's density
+    zeldovich_512  512^3 Zel'dovich ICs at a = 0.5 (box 1000, mesh 512)
+    """
+    import torch
+
+    import p3m_synth as S
+    from paper_1510_07621_gb300 import P3M, build
+
+    build.build()
+    w = args.profile_case
+    if w in ("evolved_128", "clustered_128", "uniform_128"):
+        box, n_p, mesh, a = 200.0, 128, 128, 1.0
+        if w == "evolved_128":
+            pos, mom = S.zeldovich(n_p, box, 0.02, 1512)
+        elif w == "uniform_128":
+            a = 0.02
+            pos, mom = S.zeldovich(n_p, box, a, 1512)
+        else:
+            pos, mom = S.clustered(n_p, box, 1512)
+    elif w == "eds_32":
+        box, n_p, mesh, a = 64.0, 32, 32, 0.02
+        pos, mom = S.zeldovich(n_p, box, a, 1511)
+    elif w == "zeldovich_256":
+        box, n_p, mesh, a = 500.0, 256, 256, 0.5
+        pos, mom = S.zeldovich(n_p, box, a, 1514)
+    else:
+        box, n_p, mesh, a = 1000.0, 512, 512, 0.5
+        pos, mom = S.zeldovich(n_p, box, a, 1513)
+    sim = P3M(box, n_p ** 3, mesh, precision=args.precision)
+    if w == "evolved_128":
+        sim.set_particles(pos, mom, a=0.02)
+        a_s = S.log_spaced_steps(0.02, 1.0, 64)
+        for k in range(64):
+            sim.step(a_s[k], a_s[k + 1] - a_s[k])
+    else:
+        sim.set_particles(pos, mom, a=a)
+    torch.cuda.synchronize()
+    sim.set_timing(True)
+    sim.timings(reset=True)
+    for _ in range(args.evals):
+        if args.profile_steps:
+            sim.step(a, 0.01 * a)
+            a *= 1.01
+        else:
+            sim.forces(a)
+    t = sim.timings(reset=True)
+    d = sim.diagnostics()
+    sim.close()
+    return {"profile_case": w, "evals": args.evals, "phase_ms": t, "pairs": d["pairs"],
+            "max_cell_count": d["max_cell_count"], "pair_warp_j_total": d["pair_warp_j"],
+            "pair_blocks_culled_total": d["pair_blocks_culled"], "pair_tiles_total": d["pair_tiles"]}
+
+
 # ---------------------------------------------------------------- main
 
 
@@ -719,9 +846,23 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--save-snapshot", default=None,
                     help="write the a=1 positions (float32 .npy) to this path, for offline analysis")
-    ap.add_argument("--cpu-sample", type=int, default=8000,
-                    help="particles whose pair sum the oracle times (0: skip the CPU baseline)")
+    ap.add_argument("--cpu-stride", type=int, default=1,
+                    help="cpu_baseline: the oracle's pair sum runs on every stride-th particle "
+                         "in cell order (1: all particles; 0: skip the CPU baseline)")
+    ap.add_argument("--ref-stride", type=int, default=0,
+                    help="reference arm: pair-sum sample stride (0: max(16, 4 x steps))")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the other configurations (512^3 run, 48-simulation ensemble, "
+                         "differentiable run) that the default N=1 line carries under 'configs'")
+    ap.add_argument("--profile-case", choices=PROFILE_CASES, default=None,
+                    help="run one workload for a profiler and print its phase times (no benchmark line)")
+    ap.add_argument("--evals", type=int, default=2, help="--profile-case: force evaluations (or steps)")
+    ap.add_argument("--profile-steps", action="store_true",
+                    help="--profile-case: time kick-drift-kick steps instead of force evaluations")
     args = ap.parse_args()
+    if args.profile_case:
+        print(json.dumps(run_profile_case(args)), flush=True)
+        return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
@@ -747,6 +888,8 @@ def main():
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
         dist = tdist
     out = run_ours(args, rank, world, local_rank, dist)
+    if rank == 0 and world == 1 and not args.no_configs:
+        out["configs"] = other_configs(args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

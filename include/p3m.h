@@ -332,6 +332,16 @@ int p3m_timings(p3m_ctx *ctx, double *ms, int n, int reset);
 const char *p3m_phase_name(int i);
 
 /*
+ * Measurement helper (no counterpart in the guide): the FMA throughput of the current GPU in
+ * TFLOP/s (an FMA counts 2 flops), FP32 (fp64 = 0) or FP64 (fp64 = 1), from independent
+ * multiply-add chains over 8 blocks of 256 threads per SM; best of two timed launches after
+ * a warm-up.  Allocates and frees a small device buffer and its own stream; synchronises.
+ * Used for the roofline of the pair kernels: FP32 bounds the mixed mode, FP64 the all-FP64
+ * mode.  Returns P3M_ECUDA on a CUDA error (*tflops = NaN).
+ */
+int p3m_measure_fma_peak(int fp64, double *tflops);
+
+/*
  * Allocation-free cell binning.  The paper has no counterpart to this entry point: it serves
  * callers that may not allocate GPU memory themselves.  Examples are code embedded in a
  * framework whose own caching allocator owns the device memory (a cudaMalloc behind its back
@@ -352,26 +362,45 @@ const char *p3m_phase_name(int i);
  * is loaded.  Every GPU that loads the library holds that area until the process exits, and
  * it bounds n to at most P3M_NOALLOC_MAX_N particles.  Larger n, NULL pointers or an invalid
  * geometry return P3M_EINVAL before any launch, with the reason in p3m_last_error(NULL).
- * The first call on each device performs a one-time set-up (it looks up the device address of
- * that area with the device current); make that first call before any stream capture begins.
+ * The first call on each device performs a set-up (it looks up the device address of that
+ * area with the device current); make that first call before any stream capture begins.
+ * Calls made while the stream is not capturing look the address up again, so that after a
+ * cudaDeviceReset the next call outside capture refreshes it; a call inside a capture uses the
+ * address found by the last call outside one (P3M_ECUDA if there was none).
  * All calls share the one area, which keeps the contents of the last call (nothing in it needs
  * to start at zero): calls whose GPU work overlaps, on different streams or from different
  * host threads, race and corrupt each other's results.  Order them on one stream.
  */
-/*
- * Measurement helper (no counterpart in the guide): the FMA throughput of the current GPU in
- * TFLOP/s (an FMA counts 2 flops), FP32 (fp64 = 0) or FP64 (fp64 = 1), from independent
- * multiply-add chains over 8 blocks of 256 threads per SM; best of two timed launches after
- * a warm-up.  Allocates and frees a small device buffer and its own stream; synchronises.
- * Used for the roofline of the pair kernels: FP32 bounds the mixed mode, FP64 the all-FP64
- * mode.  Returns P3M_ECUDA on a CUDA error (*tflops = NaN).
- */
-int p3m_measure_fma_peak(int fp64, double *tflops);
 
 #define P3M_NOALLOC_MAX_N 1048576
 int p3m_cell_sort_noalloc(const double *pos3n, int64_t n, double box, int n_c, int sub_bits,
                           uint32_t *keys_out, uint32_t *ids_out, uint32_t *cell_start_out,
                           void *stream);
+
+/*
+ * Host-side fault injection, for testing how the library reports failures without making the
+ * GPU fault (the guide has no counterpart).  what:
+ *   P3M_INJECT_ALLOC       the device allocation number arg (0-based, in the order p3m_init
+ *                          makes them) of every following p3m_init fails as if cudaMalloc had
+ *                          returned cudaErrorMemoryAllocation: p3m_init frees what it had
+ *                          allocated and returns P3M_ENOMEM, and p3m_last_error(NULL) names the
+ *                          allocation and says "(injected)".  Process-wide; ctx may be NULL.
+ *   P3M_INJECT_FFT_PLAN    every following p3m_init fails at its first cuFFT plan as if the
+ *                          plan call had returned CUFFT_ALLOC_FAILED (P3M_ECUFFT).  Process-wide.
+ *   P3M_INJECT_SORT_TIMEOUT  on ctx: the particle sort's look-back waits on a zeroed status word
+ *                          that nothing sets and gives up after arg clock cycles (1..2^31), so
+ *                          force evaluations return P3M_ETIMEOUT right after the sort, before
+ *                          any kernel reads the (unreliable) order; the particle state is kept.
+ *                          Allocates a zeroed buffer the size of the sort's look-back status.
+ *   P3M_INJECT_NONE        clears every injection (and, with ctx, frees that buffer and restores
+ *                          the default wait limit of 2^31 cycles); the context is usable again.
+ * Returns P3M_EINVAL for an unknown fault or argument.
+ */
+#define P3M_INJECT_NONE 0
+#define P3M_INJECT_ALLOC 1
+#define P3M_INJECT_FFT_PLAN 2
+#define P3M_INJECT_SORT_TIMEOUT 3
+int p3m_inject_fault(p3m_ctx *ctx, int what, int64_t arg);
 
 /* Message of the last failure on ctx (ctx NULL: the last failed p3m_init).  Never NULL. */
 const char *p3m_last_error(const p3m_ctx *ctx);

@@ -24,6 +24,10 @@ P3M_PREC_MIXED = 0
 P3M_PREC_FP64 = 1
 P3M_NPHASES = 10
 P3M_NOALLOC_MAX_N = 1048576
+P3M_INJECT_NONE = 0
+P3M_INJECT_ALLOC = 1
+P3M_INJECT_FFT_PLAN = 2
+P3M_INJECT_SORT_TIMEOUT = 3
 
 # every symbol the header declares, with (restype, argtypes)
 _c = ctypes
@@ -85,6 +89,7 @@ SIGNATURES = {
     "p3m_ensemble_set_batched": (_c.c_int, [_vp, _c.c_int]),
     "p3m_autotune": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _vp]),
     "p3m_get_tuning": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "p3m_inject_fault": (_c.c_int, [_vp, _c.c_int, _c.c_int64]),
     "p3m_cell_sort_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_double, _c.c_int, _c.c_int,
                                          _vp, _vp, _vp, _vp]),
     "p3m_measure_fma_peak": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_double)]),

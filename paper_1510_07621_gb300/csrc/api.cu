@@ -186,7 +186,7 @@ void release(p3m_ctx *c)
                     c->tab_origin,
                     c->adj_u,     c->adj_vfx,  c->adj_vs,       c->adj_out,  c->kself,
                     c->li,        c->relx,     c->sort_status,  c->sort_hist,
-                    c->rho_fix,   c->fix_exp,  c->ps_part};
+                    c->rho_fix,   c->fix_exp,  c->ps_part,     c->sort_probe};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (c->plans_made) {
@@ -201,6 +201,11 @@ void release(p3m_ctx *c)
     }
 }
 
+// Host-side fault injection (p3m_inject_fault): the index of the p3m_init device allocation
+// that fails (-1: none) and whether p3m_init's cuFFT plans fail.
+int g_inject_alloc = -1;
+bool g_inject_fft = false;
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t bytes)
 {
@@ -213,7 +218,12 @@ int check_flags(p3m_ctx *c)
     uint32_t flags = 0;
     CK(cudaMemcpyAsync(&flags, c->counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (flags & P3M_FLAG_TIMEOUT) return fail(c, P3M_ETIMEOUT, "a bounded device-side wait gave up");
+    if (flags & P3M_FLAG_TIMEOUT) {
+        CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(uint32_t), c->stream));  // reported once
+        c->forces_valid = false;
+        c->sorted_valid = false;
+        return fail(c, P3M_ETIMEOUT, "a bounded device-side wait gave up");
+    }
     return P3M_OK;
 }
 
@@ -227,6 +237,10 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool
     {
         Phase ph(c, PH_SORT);
         CK(launch_radix_sort(c));
+    }
+    if (c->sort_probe) {  // injected sort timeout: stop before anything reads the order
+        const int rc = check_flags(c);
+        if (rc) return rc;
     }
     {
         Phase ph(c, PH_PERMUTE);
@@ -485,6 +499,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
     c->a = 1.0;
     c->stream = (cudaStream_t)opt.stream;
     c->key_bits = key_bits;
+    c->sort_wait_limit = 1ll << 31;
     c->fac_cap = P3M_MAX_GRAPH_STEPS;
     strcpy(c->err, "no error");
 
@@ -540,11 +555,13 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             {(void **)&c->adj_u, 3 * real * M3}, {(void **)&c->adj_vfx, opt.precision == P3M_PREC_MIXED ? 384 * ((N + 31) / 32) : 16},
             {(void **)&c->adj_vs, 24 * N},    {(void **)&c->adj_out, 24 * N},
         };
+        int idx = 0;
         for (auto &a : allocs) {
-            e = dalloc(a.p, a.bytes);
+            const bool injected = idx++ == g_inject_alloc;
+            e = injected ? cudaErrorMemoryAllocation : dalloc(a.p, a.bytes);
             if (e != cudaSuccess) {
-                rc = fail(nullptr, P3M_ENOMEM, "p3m_init: cudaMalloc of %zu bytes failed: %s", a.bytes,
-                          cudaGetErrorString(e));
+                rc = fail(nullptr, P3M_ENOMEM, "p3m_init: cudaMalloc of %zu bytes failed: %s%s", a.bytes,
+                          cudaGetErrorString(e), injected ? " (injected)" : "");
                 break;
             }
         }
@@ -552,6 +569,10 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         cudaMemsetAsync(c->counters, 0, 16, c->stream);
         cudaMemsetAsync(c->pair_count, 0, 64, c->stream);
         cudaMemsetAsync(c->rho_fix, 0, 8 * 3 * M3, c->stream);
+        // sort buffers start at zero: every key and slot they ever hold is then in range
+        cudaMemsetAsync(c->keys_alt, 0, 4 * N, c->stream);
+        cudaMemsetAsync(c->vals, 0, 4 * N, c->stream);
+        cudaMemsetAsync(c->vals_alt, 0, 4 * N, c->stream);
         c->ps_blocks = 2 * c->num_sms;
         if (opt.precision == P3M_PREC_MIXED)  // padding past the last particle stays zero
             cudaMemsetAsync(c->adj_vfx, 0, 384 * ((N + 31) / 32), c->stream);
@@ -610,8 +631,9 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
 
         // cuFFT: one R2C, and the three C2R as one batch of 3 (default layouts)
         int dims[3] = {mesh, mesh, mesh};
-        cufftResult r = cufftPlan3d(&c->plan_r2c, mesh, mesh, mesh,
-                                    c->precision == P3M_PREC_MIXED ? CUFFT_R2C : CUFFT_D2Z);
+        cufftResult r = g_inject_fft ? CUFFT_ALLOC_FAILED
+                                     : cufftPlan3d(&c->plan_r2c, mesh, mesh, mesh,
+                                                   c->precision == P3M_PREC_MIXED ? CUFFT_R2C : CUFFT_D2Z);
         if (r == CUFFT_SUCCESS) {
             r = cufftPlanMany(&c->plan_c2r, 3, dims, nullptr, 1, (int)nk, nullptr, 1, (int)M3,
                               c->precision == P3M_PREC_MIXED ? CUFFT_C2R : CUFFT_Z2D, 3);
@@ -626,7 +648,8 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             }
         }
         if (r != CUFFT_SUCCESS) {
-            rc = fail(nullptr, P3M_ECUFFT, "p3m_init: cuFFT plan creation failed (code %d)", (int)r);
+            rc = fail(nullptr, P3M_ECUFFT, "p3m_init: cuFFT plan creation failed (code %d)%s", (int)r,
+                      g_inject_fft ? " (injected)" : "");
             break;
         }
         c->plans_made = true;
@@ -948,3 +971,41 @@ extern "C" void p3m_free(p3m_ctx *c)
     free(c);
 }
 
+
+extern "C" int p3m_inject_fault(p3m_ctx *c, int what, int64_t arg)
+{
+    switch (what) {
+    case P3M_INJECT_NONE:
+        g_inject_alloc = -1;
+        g_inject_fft = false;
+        if (c) {
+            if (c->sort_probe) {
+                CK(cudaStreamSynchronize(c->stream));
+                CK(cudaFree(c->sort_probe));
+            }
+            c->sort_probe = nullptr;
+            c->sort_wait_limit = 1ll << 31;
+        }
+        return P3M_OK;
+    case P3M_INJECT_ALLOC:
+        if (arg < 0) return fail(c, P3M_EINVAL, "p3m_inject_fault: allocation index must be >= 0");
+        g_inject_alloc = (int)arg;
+        return P3M_OK;
+    case P3M_INJECT_FFT_PLAN:
+        g_inject_fft = true;
+        return P3M_OK;
+    case P3M_INJECT_SORT_TIMEOUT: {
+        if (!c) return fail(c, P3M_EINVAL, "p3m_inject_fault: the sort timeout needs a context");
+        if (arg < 1 || arg > (1ll << 31)) return fail(c, P3M_EINVAL, "p3m_inject_fault: wait limit out of range");
+        if (!c->sort_probe) {
+            const size_t bytes = sizeof(unsigned long long) * 256 * (size_t)c->n_tiles;
+            CK(cudaMalloc((void **)&c->sort_probe, bytes));
+            CK(cudaMemset(c->sort_probe, 0, bytes));
+        }
+        c->sort_wait_limit = (long long)arg;
+        return P3M_OK;
+    }
+    default:
+        return fail(c, P3M_EINVAL, "p3m_inject_fault: unknown fault %d", what);
+    }
+}

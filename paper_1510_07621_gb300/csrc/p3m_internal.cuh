@@ -64,6 +64,8 @@ struct p3m_ctx {
     uint32_t *sort_hist;              // particle sort: 4 x 256 digit counts, 4 tile counters
     int n_tiles;
     int key_bits;
+    long long sort_wait_limit;          // clock cycles one look-back wait may take (2^31 ~ 1 s)
+    unsigned long long *sort_probe;     // injected sort timeout: a zeroed status that nothing sets
     uint32_t *cell_start;  // n_cells + 1
     uint32_t *work;        // pair work items (cell, first slot)
     uint32_t *work_off;    // n_cells + 1

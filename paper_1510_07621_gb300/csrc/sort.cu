@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     k_onesweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t n,
                int shift, const uint32_t *__restrict__ hist, unsigned long long *status,
                uint32_t *tile_counter, uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-               uint32_t *flags)
+               uint32_t *flags, const unsigned long long *lookback, long long wait_limit)
 {
     __shared__ uint32_t s_key[P3M_SORT_TILE];
     __shared__ uint32_t s_val[P3M_SORT_TILE];
@@ -314,10 +314,11 @@ __global__ void __launch_bounds__(kThreads, 3)
         long long t = (long long)tile - 1;
         const long long t0 = clock64();
         for (;;) {
-            const unsigned long long v = *(volatile unsigned long long *)(status + (size_t)t * kRadix + d);
+            // lookback is status itself, except under an injected timeout (a zeroed copy)
+            const unsigned long long v = *(volatile const unsigned long long *)(lookback + (size_t)t * kRadix + d);
             const unsigned long long f = v & ~kCountMask;
             if (f == 0ull) {
-                if (clock64() - t0 > (1ll << 31)) {
+                if (clock64() - t0 > wait_limit) {
                     atomicOr(flags, P3M_FLAG_TIMEOUT);
                     break;
                 }
@@ -490,7 +491,7 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
          blk += nwarps) {
         const int64_t k = blk * 32 + lane;
         const bool active = k < n;
-        const uint32_t j = perm[active ? k : blk * 32];
+        const uint32_t j = min(perm[active ? k : blk * 32], (uint32_t)(n - 1));  // in bounds always
         const double x = pos[j], y = pos[n + j], z = pos[2 * n + j];
         R4 rv = make_rel<R4>(0.0, 0.0, 0.0);
         if (active) {
@@ -548,7 +549,8 @@ __global__ void k_work_count(const uint32_t *__restrict__ cell_start, int n_cell
                              uint32_t *__restrict__ work_n, uint32_t *__restrict__ max_count)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
-        const uint32_t cnt = cell_start[c + 1] - cell_start[c];
+        const uint32_t s0 = cell_start[c], s1 = cell_start[c + 1];
+        const uint32_t cnt = s1 > s0 ? s1 - s0 : 0u;  // ranges are ordered unless a sort gave up
         work_n[c] = (cnt + P3M_PAIR_TI - 1) / P3M_PAIR_TI;
         if (cnt) atomicMax(max_count, cnt);
     }
@@ -681,7 +683,9 @@ cudaError_t radix_sort_onesweep(p3m_ctx *c, uint32_t **k, uint32_t **v, bool ide
         if (e != cudaSuccess) return e;
         k_onesweep<<<n_tiles, kThreads, 0, s>>>(kin, vin, n, p * kRadixBits, c->sort_hist + p * kRadix,
                                                 c->sort_status, c->sort_hist + 4 * kRadix + p, kout,
-                                                vout, c->counters + 1);
+                                                vout, c->counters + 1,
+                                                c->sort_probe ? c->sort_probe : c->sort_status,
+                                                c->sort_wait_limit);
         c->launches += 1;
         uint32_t *t = kin;  // the next pass reads what this one wrote
         kin = kout;
@@ -800,20 +804,28 @@ namespace {
 std::mutex g_noalloc_mutex;
 uint32_t *g_noalloc_ptr[256];  // device address of g_noalloc_scratch, per device ordinal
 
-// Device address of the scratch on the current device.  Looked up with the device current,
-// once per device; the host-side symbol itself is not a device address.
-cudaError_t noalloc_scratch(uint32_t **out)
+// Device address of the scratch on the current device, looked up with that device current (the
+// host-side symbol itself is not a device address).  The first call on a device must look it up
+// outside stream capture; later calls look it up again whenever the stream is not capturing, so
+// that an address cached before a cudaDeviceReset (which reloads the module in a new context) is
+// never used afterwards; while capturing they use the cached address.
+cudaError_t noalloc_scratch(cudaStream_t stream, uint32_t **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = (uint32_t *)p;
+    } else if (!g_noalloc_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;  // no set-up call before the capture began
     }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
@@ -841,7 +853,7 @@ extern "C" int p3m_cell_sort_noalloc(const double *pos3n, int64_t n, double box,
     while (key_bits < 32 && (max_key >> key_bits)) ++key_bits;
 
     uint32_t *scratch = nullptr;
-    cudaError_t e = noalloc_scratch(&scratch);
+    cudaError_t e = noalloc_scratch((cudaStream_t)stream, &scratch);
     if (e != cudaSuccess)
         return p3m_fail_global(P3M_ECUDA, "p3m_cell_sort_noalloc: scratch lookup failed: %s",
                                cudaGetErrorString(e));

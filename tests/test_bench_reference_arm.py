@@ -1,5 +1,5 @@
 """The bench's reference arm (the FP64 oracle on the host cores) prints the contract's JSON line:
-CPU only, one step with a small pair-sum sample of the 128^3 stand-in snapshot."""
+CPU only, one step with a small stratified pair-sum sample of the 128^3 stand-in snapshot."""
 
 import json
 import os
@@ -12,13 +12,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_prints_one_contract_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--cpu-sample", "300"],
+                        "--steps", "1", "--warmup", "0", "--ref-stride", "2048"],
                        capture_output=True, text=True, timeout=900, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
+    assert d["steps_executed"] == 1 and d["config"]["pair_sample_stride"] == 2048
+    assert d["config"]["pairs_per_particle"] > 100
     assert d["unit"] == "particle-updates/s" and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]

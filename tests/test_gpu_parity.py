@@ -203,10 +203,12 @@ def test_momentum_conservation(P3M):
 
 @pytest.mark.parametrize("precision,tol,mtol", [("fp64", 1e-11, 1e-9), ("mixed", 1e-6, 1e-4)])
 def test_ten_steps_eds32(P3M, precision, tol, mtol):
-    """Config of the 32^3 EdS run (an FP64 configuration): 10 log-spaced steps a = 0.02 -> 0.1,
-    every position within 1e-6 L of the oracle's.  The mixed mode is held to the same bar in
-    rms; its worst particle (a close pair, whose FP32 separation carries ~1e-6 absolute error)
-    must stay within 1e-5 L."""
+    """Config of the 32^3 EdS run: 10 log-spaced steps a = 0.02 -> 0.1 against the oracle.
+    FP64 mode: every position within 1e-11 L.  Mixed mode: RMS displacement within 1e-6 L; the
+    worst particle within 4e-6 L, the band in which the FP64 oracle's own worst particle moves
+    when its forces carry noise of the FP32 path's measured relative size (3.4e-6 RMS): a
+    1e-6 L bound on the worst particle needs force errors below about 1e-6
+    (tests/test_trajectory_sensitivity.py)."""
     pos, mom, kw = _case("eds32")
     n = pos.shape[1]
     a_s = S.log_spaced_steps(0.02, 0.1, 10)
@@ -227,7 +229,7 @@ def test_ten_steps_eds32(P3M, precision, tol, mtol):
         assert np.max(np.abs(dx)) <= tol * kw["box"]
     else:
         assert math.sqrt(np.mean(dx * dx)) <= tol * kw["box"]
-        assert np.max(np.abs(dx)) <= 10 * tol * kw["box"]
+        assert np.max(np.abs(dx)) <= 4e-6 * kw["box"]
     assert math.sqrt(np.mean((gmom - m) ** 2)) <= mtol * math.sqrt(np.mean(m * m))
     # the reductions of the diagnostics against numpy sums of the returned momenta
     assert np.allclose(d["momentum"], gmom.sum(axis=1), rtol=0, atol=1e-12 * np.abs(gmom).sum())
@@ -238,7 +240,8 @@ def test_ten_steps_eds32(P3M, precision, tol, mtol):
 def test_step_with_supplied_forces_equals_recompute(P3M):
     """A state loaded with its accelerations steps like one that recomputes them: identical
     positions (the drift only uses the supplied forces); momenta equal up to the FP32 rounding
-    of the new forces (float atomics in the deposit and the tie order inside cells differ)."""
+    of the new forces (the two runs sort from different slot orders, so equal keys keep
+    different orders and the pair sums add in different orders)."""
     pos, mom, kw = _case("eds32")
     n = pos.shape[1]
     with P3M(kw["box"], n, kw["mesh"]) as sim:
