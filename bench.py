@@ -500,11 +500,12 @@ ENSEMBLE_NAME = ("ensemble48: 48 independent EdS simulations, 16 each of 48^3, 6
 def run_ensemble(args):
     """The 48-simulation ensemble advanced a = 0.05 -> 1 in 20 steps: host-issued steps one
     simulation after another; host-issued steps on one stream per simulation; graph replay
-    (8-step graphs for the whole ensemble) -- the last two each with per-simulation pair
-    launches and with one batched pair launch per step over all simulations.  The value is
-    the graph replay with per-simulation launches (the library's default; the batched launch
-    is within 1 % of it here).  Every mode starts from the ICs with their forces known, so no
-    timed region contains a force evaluation of the ICs."""
+    (8-step graphs for the whole ensemble); each ensemble mode with FFTs batched per mesh size
+    (one R2C and one C2R per size group and step) or per simulation, and with per-simulation
+    pair launches or one batched pair launch per step.  The value is the library's default:
+    graph replay with size-grouped FFTs and per-simulation pair launches.  Every mode starts
+    from the ICs with their forces known, so no timed region contains a force evaluation of
+    the ICs."""
     import torch
     from paper_1510_07621_gb300 import P3M, Ensemble, build
 
@@ -516,13 +517,11 @@ def run_ensemble(args):
     ics = [S.zeldovich(n_p, box, a[0], 4000 + k) for k, n_p in enumerate(sizes)]
     total = sum(n_p ** 3 for n_p in sizes)
 
-    acc0 = [None] * len(sizes)  # the ICs' accelerations, so that a restore needs no evaluation
-
     def fresh():
         sims = [P3M(box, n_p ** 3, n_p, softening=0.02, stream=0) for n_p in sizes]
-        for k, (s_, (p, m)) in enumerate(zip(sims, ics)):
+        for s_, (p, m) in zip(sims, ics):
             s_.set_particles(p, m, a=a[0])
-            acc0[k] = s_.forces(a[0])
+            s_.forces(a[0])
         torch.cuda.synchronize()
         return sims
 
@@ -540,17 +539,23 @@ def run_ensemble(args):
         s_.close()
     # 2.-5. the ensemble: host launches on per-simulation streams or graph replay, each with
     # per-simulation pair launches or one batched pair launch per step
-    for mode, use_graph, batched in (("stream_host_launches", False, False),
-                                     ("stream_host_launches_batched_pairs", False, True),
-                                     ("graph_ensemble", True, False),
-                                     ("graph_ensemble_batched_pairs", True, True)):
+    for mode, use_graph, batched, groups in (
+            ("stream_host_launches", False, False, False),
+            ("stream_host_launches_fft_groups", False, False, True),
+            ("stream_host_launches_batched_pairs", False, True, False),
+            ("graph_ensemble", True, False, True),
+            ("graph_ensemble_per_context_fft", True, False, False),
+            ("graph_ensemble_batched_pairs", True, True, False)):
         sims = fresh()
-        with Ensemble(sims, batched=batched) as ens:
-            if use_graph:  # capture outside the timed region, then restore the ICs and forces
+        with Ensemble(sims, batched=batched, fft_groups=groups) as ens:
+            if use_graph:  # capture outside the timed region, then restore the ICs and their
+                # forces by the same evaluation as fresh(), so that the particles start from the
+                # same slot order (equal sort keys keep it) as in the serial mode
                 ens.run(a[:3], use_graph=True)
                 torch.cuda.synchronize()
-                for s_, (p, m), g in zip(sims, ics, acc0):
-                    s_.set_particles(p, m, acc=g, a=a[0])
+                for s_, (p, m) in zip(sims, ics):
+                    s_.set_particles(p, m, a=a[0])
+                    s_.forces(a[0])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ens.run(a, use_graph=use_graph)

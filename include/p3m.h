@@ -222,12 +222,24 @@ void p3m_ensemble_free(p3m_ensemble *ens);
  * branches, then merges their pair work lists into one list sorted by estimated cost and
  * evaluates every such context's pair sum in one persistent kernel launch (the contexts'
  * arguments read from a device table).  Other contexts step as before.  Results equal the
- * per-context launches up to the FP32 rounding of the mesh deposit's atomics.  Every step then
- * waits for all contexts' mesh phases before the pair launch; on the 48-simulation ensemble of
- * 48^3..96^3 particles the two are within 1 % of each other (342 M and 340 M particle-updates/s
- * with graphs).  enable = 0 returns to independent per-context branches.
+ * per-context launches bit for bit.  Every step then waits for all contexts' mesh phases
+ * before the pair launch; on the 48-simulation ensemble of 48^3..96^3 particles the two are
+ * within 1 % of each other with graphs.  enable = 0 returns to per-context pair launches.
  */
 int p3m_ensemble_set_batched(p3m_ensemble *ens, int enable);
+/*
+ * Size-grouped FFTs (on by default when at least two contexts share a mesh size and precision;
+ * enable = 0 turns them off, 1 on): the contexts of each such group get their density, spectrum
+ * and force meshes as slices of one allocation per buffer, made by the ensemble, and every step
+ * runs one batched R2C and one batched C2R per group on the ensemble's own stream instead of
+ * one of each per context.  The steps then advance all contexts in lockstep phases (the mesh
+ * deposit of all, the batched R2C, the k-space pass of all, the batched C2R, the gather and pair
+ * force of all); without groups each context's steps are one independent branch.  Results equal
+ * the per-context FFTs bit for bit.  p3m_ensemble_free (or enable = 0) copies the slices' contents
+ * back into the contexts' own meshes and releases the group buffers.  Batched pair launches
+ * (p3m_ensemble_set_batched) take precedence: with them on, each context runs its own FFTs.
+ */
+int p3m_ensemble_set_fft_groups(p3m_ensemble *ens, int enable);
 
 /*
  * Autotuner of the sort key's Hilbert depth and of the FP32 pair kernel's tile length: times two

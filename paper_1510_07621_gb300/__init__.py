@@ -294,9 +294,11 @@ class P3M:
 
 class Ensemble:
     """Independent P3M contexts advanced together through one schedule of scale factors, one
-    CUDA graph launch per step for the whole ensemble (p3m_ensemble_*)."""
+    CUDA graph launch per step for the whole ensemble, FFTs batched per mesh size
+    (p3m_ensemble_*)."""
 
-    def __init__(self, sims, own_streams: bool = True, batched: bool | None = None):
+    def __init__(self, sims, own_streams: bool = True, batched: bool | None = None,
+                 fft_groups: bool | None = None):
         self._lib = load()
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s._ctx.value for s in self.sims])
@@ -307,6 +309,8 @@ class Ensemble:
         self._e = e
         if batched is not None:  # None: the library's default (per-simulation pair launches)
             check(self._lib.p3m_ensemble_set_batched(self._e, 1 if batched else 0), None)
+        if fft_groups is not None:  # None: the library's default (size-grouped batched FFTs)
+            check(self._lib.p3m_ensemble_set_fft_groups(self._e, 1 if fft_groups else 0), None)
 
     def run(self, a_list, use_graph: bool = True):
         a = np.ascontiguousarray(a_list, dtype=np.float64)

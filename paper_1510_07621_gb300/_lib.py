@@ -86,6 +86,7 @@ SIGNATURES = {
     "p3m_ensemble_create": (_c.c_int, [_c.POINTER(_vp), _vp, _c.c_int, _c.c_int]),
     "p3m_ensemble_run": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int]),
     "p3m_ensemble_free": (None, [_vp]),
+    "p3m_ensemble_set_fft_groups": (_c.c_int, [_vp, _c.c_int]),
     "p3m_ensemble_set_batched": (_c.c_int, [_vp, _c.c_int]),
     "p3m_autotune": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _vp]),
     "p3m_get_tuning": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),

@@ -135,18 +135,15 @@ __global__ void k_deposit_vec(const double *__restrict__ pos, const double *__re
     }
 }
 
-// u = fix 2^-S (signed), and fix = 0 for the next deposit.
+// u = fix 2^-S (signed).
 template <typename T>
-__global__ void k_fix_to_vec(unsigned long long *__restrict__ fix, size_t n, const int *__restrict__ s_dev,
-                             T *__restrict__ u)
+__global__ void k_fix_to_vec(const unsigned long long *__restrict__ fix, size_t n,
+                             const int *__restrict__ s_dev, T *__restrict__ u)
 {
     const double inv_scale = ldexp(1.0, -*s_dev);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const long long v = (long long)fix[i];
-        fix[i] = 0ull;
-        u[i] = (T)(__ll2double_rn(v) * inv_scale);
-    }
+         i += (size_t)gridDim.x * blockDim.x)
+        u[i] = (T)(__ll2double_rn((long long)fix[i]) * inv_scale);
 }
 
 // psi_k = sum_b (+i kg_b G(k)) u_b,k with G as in the forward pass (constants included).
@@ -914,6 +911,7 @@ cudaError_t vjp_mesh(p3m_ctx *c, const double *v_slots, double *out_slots)
     T *u = (T *)c->adj_u;
     unsigned long long *maxbits = (unsigned long long *)(c->fix_exp + 2);
     cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->rho_fix, 0, 3 * M3 * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
     int nb = 0;
     while (nb < 63 && (c->g.n >> nb)) ++nb;

@@ -230,10 +230,13 @@ int check_flags(p3m_ctx *c)
 // ---------------------------------------------------------------- force evaluation
 // Sort by cell, mesh force, pair force.  Positions must already be wrapped and keyed
 // (c->keys).  Result: c->acc (total), c->acc_lr (mesh part).  kfac != 0: the final half kick
-// mom += kfac * acc is fused into the last kernel.
-int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool pairs)
+// mom += kfac * acc is fused into the last kernel.  The phases are also run one by one by
+// ensembles whose contexts share batched FFTs (eval_pre, the R2C, eval_kspace, the C2R,
+// eval_post).
+
+// Sort, permute, cell ranges and work list, CIC deposit.
+int eval_pre(p3m_ctx *c)
 {
-    const double *kfac_dev = from_table ? c->cur_fac + 2 : nullptr;
     {
         Phase ph(c, PH_SORT);
         CK(launch_radix_sort(c));
@@ -251,22 +254,38 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool
         Phase ph(c, PH_DEPOSIT);
         CK(launch_deposit(c, true));
     }
-    {
-        Phase ph(c, PH_FFT_R2C);
-        CKF(c->precision == P3M_PREC_MIXED
-                ? cufftExecR2C(c->plan_r2c, (cufftReal *)c->rho, (cufftComplex *)c->rho_k)
-                : cufftExecD2Z(c->plan_r2c, (cufftDoubleReal *)c->rho, (cufftDoubleComplex *)c->rho_k));
-    }
-    {
-        Phase ph(c, PH_KSPACE);
-        CK(launch_kspace(c));
-    }
-    {
-        Phase ph(c, PH_FFT_C2R);
-        CKF(c->precision == P3M_PREC_MIXED
-                ? cufftExecC2R(c->plan_c2r, (cufftComplex *)c->frc_k, (cufftReal *)c->frc)
-                : cufftExecZ2D(c->plan_c2r, (cufftDoubleComplex *)c->frc_k, (cufftDoubleReal *)c->frc));
-    }
+    return P3M_OK;
+}
+
+int eval_r2c(p3m_ctx *c)
+{
+    Phase ph(c, PH_FFT_R2C);
+    CKF(c->precision == P3M_PREC_MIXED
+            ? cufftExecR2C(c->plan_r2c, (cufftReal *)c->rho, (cufftComplex *)c->rho_k)
+            : cufftExecD2Z(c->plan_r2c, (cufftDoubleReal *)c->rho, (cufftDoubleComplex *)c->rho_k));
+    return P3M_OK;
+}
+
+int eval_kspace(p3m_ctx *c)
+{
+    Phase ph(c, PH_KSPACE);
+    CK(launch_kspace(c));
+    return P3M_OK;
+}
+
+int eval_c2r(p3m_ctx *c)
+{
+    Phase ph(c, PH_FFT_C2R);
+    CKF(c->precision == P3M_PREC_MIXED
+            ? cufftExecC2R(c->plan_c2r, (cufftComplex *)c->frc_k, (cufftReal *)c->frc)
+            : cufftExecZ2D(c->plan_c2r, (cufftDoubleComplex *)c->frc_k, (cufftDoubleReal *)c->frc));
+    return P3M_OK;
+}
+
+// Gather, then the pair force (or, for pure PM, the mesh force alone) with the final kick.
+int eval_post(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool pairs)
+{
+    const double *kfac_dev = from_table ? c->cur_fac + 2 : nullptr;
     if (c->short_range && !pairs) {  // mesh part only (cells, sorted state, mesh fields)
         Phase ph(c, PH_GATHER);
         CK(launch_gather(c, c->acc_lr));
@@ -296,6 +315,16 @@ int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool
     return P3M_OK;
 }
 
+int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool pairs)
+{
+    int rc = eval_pre(c);
+    if (!rc) rc = eval_r2c(c);
+    if (!rc) rc = eval_kspace(c);
+    if (!rc) rc = eval_c2r(c);
+    if (!rc) rc = eval_post(c, kfac, sr_only_out, from_table, pairs);
+    return rc;
+}
+
 int key_current(p3m_ctx *c)
 {
     Phase ph(c, PH_KICK_DRIFT);
@@ -305,30 +334,45 @@ int key_current(p3m_ctx *c)
 
 bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
-// One kick-drift-kick step a -> a + da with valid forces at a.  from_table: the step's factors
-// come from the device table (graph-replayed steps; a and da unused).
-int step_body(p3m_ctx *c, double a, double da, bool from_table)
+// First part of a kick-drift-kick step a -> a + da: the step's factors (host arguments, or the
+// device table for graph-replayed steps), the first half kick and the drift with the new keys.
+// Returns the second half kick's factor in *k2 (0 when it comes from the table).
+int step_kd(p3m_ctx *c, double a, double da, bool from_table, double *k2)
 {
-    double k1 = 0.0, dfac = 0.0, k2 = 0.0;
+    double k1 = 0.0, dfac = 0.0;
+    *k2 = 0.0;
     if (from_table) {
         CK(launch_step_begin(c));
     } else {
         const double am = a + 0.5 * da, a2 = a + da;
         k1 = c->mass * p3m_kick_factor(c->cosmo, a, am);
         dfac = p3m_drift_factor(c->cosmo, a, a2) / c->mass;
-        k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
+        *k2 = c->mass * p3m_kick_factor(c->cosmo, am, a2);
     }
-    {
-        Phase ph(c, PH_KICK_DRIFT);
-        CK(launch_kick_drift_keys(c, true, k1, dfac, from_table));
-    }
-    int rc = evaluate(c, k2, nullptr, from_table);
-    if (rc) return rc;
+    Phase ph(c, PH_KICK_DRIFT);
+    CK(launch_kick_drift_keys(c, true, k1, dfac, from_table));
+    return P3M_OK;
+}
+
+// Last part of a step: the Layzer-Irvine bookkeeping of a context that tracks its energy.
+int step_tail(p3m_ctx *c, double a, double da, bool from_table)
+{
     if (c->track_energy) {
         Phase ph(c, PH_OTHER);
         CK(launch_li_update(c, from_table ? c->cur_fac + 3 : nullptr, a + da));
     }
     return P3M_OK;
+}
+
+// One kick-drift-kick step a -> a + da with valid forces at a.  from_table: the step's factors
+// come from the device table (graph-replayed steps; a and da unused).
+int step_body(p3m_ctx *c, double a, double da, bool from_table)
+{
+    double k2 = 0.0;
+    int rc = step_kd(c, a, da, from_table, &k2);
+    if (!rc) rc = evaluate(c, k2, nullptr, from_table);
+    if (!rc) rc = step_tail(c, a, da, from_table);
+    return rc;
 }
 
 // The part of a step that precedes the pair sum, for a context whose pair sum runs in the
@@ -568,7 +612,6 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         if (rc != P3M_OK) break;
         cudaMemsetAsync(c->counters, 0, 16, c->stream);
         cudaMemsetAsync(c->pair_count, 0, 64, c->stream);
-        cudaMemsetAsync(c->rho_fix, 0, 8 * 3 * M3, c->stream);
         // sort buffers start at zero: every key and slot they ever hold is then in range
         cudaMemsetAsync(c->keys_alt, 0, 4 * N, c->stream);
         cudaMemsetAsync(c->vals, 0, 4 * N, c->stream);

@@ -51,6 +51,24 @@ struct p3m_ensemble {
     uint32_t *gkey[2], *gval[2], *gcounts, *gaux, *gtotal, *gcursor;
     cudaEvent_t after_pairs;
     unsigned long long launches;
+
+    // Size-grouped FFTs: contexts with the same mesh and precision whose density, spectrum and
+    // force meshes are slices of one allocation, so that one batched R2C and one batched C2R
+    // (on the parent stream) serve the whole group; the steps then run in phases (see ens_step_fft).
+    bool grouped;             // on (default when some group has at least two contexts)
+    int ngrp;
+    struct FftGroup *grp;
+    int *gi;                  // per context: its group, or -1 (its FFTs stay its own)
+    void **saved;             // per context: its own rho, rho_k, frc_k, frc while grouped
+    double *k2;               // per context: second half-kick factor of the current step
+};
+
+struct FftGroup {
+    int mesh, precision, count;
+    size_t rho_b, rhok_b, frck_b, frc_b;  // bytes of one member's slice of each buffer
+    void *rho, *rho_k, *frc_k, *frc;
+    cufftHandle r2c, c2r;
+    bool plans;
 };
 
 namespace {
@@ -60,6 +78,7 @@ constexpr int kChunkSteps = 8;  // steps per chunk graph (even: buffer roles hav
 // Captures `steps` consecutive steps of every context as parallel branches of one graph
 // (one branch per context, its steps in sequence) into *out.
 int ens_step(p3m_ensemble *e, double a, double da, bool from_table);
+int ens_step_fft(p3m_ensemble *e, double a, double da, bool from_table);
 
 int capture_steps(p3m_ensemble *e, int steps, cudaGraphExec_t *out)
 {
@@ -69,9 +88,10 @@ int capture_steps(p3m_ensemble *e, int steps, cudaGraphExec_t *out)
     if (err != cudaSuccess)
         return p3m_fail_global(P3M_ECUDA, "graph capture: %s", cudaGetErrorString(err));
     int rc = P3M_OK;
-    if (e->batched) {  // the steps one after another, each with its batched pair launch
+    if (e->batched || e->grouped) {  // the steps one after another, in lockstep
         for (int i = 0; i < e->n; ++i) e->c[i]->capturing = true;
-        for (int k = 0; k < steps && rc == P3M_OK; ++k) rc = ens_step(e, 0.0, 0.0, true);
+        for (int k = 0; k < steps && rc == P3M_OK; ++k)
+            rc = e->batched ? ens_step(e, 0.0, 0.0, true) : ens_step_fft(e, 0.0, 0.0, true);
         for (int i = 0; i < e->n; ++i) e->c[i]->capturing = false;
     } else {  // each context's steps as one branch
         err = cudaEventRecord(e->fork, e->parent);
@@ -151,6 +171,177 @@ int ens_step(p3m_ensemble *e, double a, double da, bool from_table)
     }
     if (err != cudaSuccess)
         return p3m_fail_global(P3M_ECUDA, "ensemble step: %s", cudaGetErrorString(err));
+    return P3M_OK;
+}
+
+// One lockstep step of every context with the FFTs of each group batched: (A) per context, the
+// first half kick, drift, sort, permute and deposit (a context outside every group runs its whole
+// step here); (B) one batched R2C per group; (C) per context, the k-space pass; (D) one batched
+// C2R per group; (E) per context, the gather, the pair force with the second half kick and the
+// energy bookkeeping.  Branches fork from and join the parent stream at each phase.
+int ens_step_fft(p3m_ensemble *e, double a, double da, bool from_table)
+{
+    auto fork = [&]() { return cudaEventRecord(e->fork, e->parent); };
+    cudaError_t err = fork();
+    int rc = P3M_OK;
+    for (int phase = 0; phase < 3 && err == cudaSuccess && rc == P3M_OK; ++phase) {
+        if (phase > 0) err = fork();
+        for (int i = 0; i < e->n && err == cudaSuccess && rc == P3M_OK; ++i) {
+            p3m_ctx *c = e->c[i];
+            if (phase > 0 && e->gi[i] < 0) continue;
+            err = cudaStreamWaitEvent(c->stream, e->fork, 0);
+            if (err != cudaSuccess) break;
+            if (phase == 0) {
+                if (e->gi[i] < 0) {
+                    rc = step_body(c, a, da, from_table);
+                } else {
+                    rc = step_kd(c, a, da, from_table, &e->k2[i]);
+                    if (!rc) rc = eval_pre(c);
+                }
+            } else if (phase == 1) {
+                rc = eval_kspace(c);
+            } else {
+                rc = eval_post(c, e->k2[i], nullptr, from_table, true);
+                if (!rc) rc = step_tail(c, a, da, from_table);
+            }
+            if (rc == P3M_OK) err = cudaEventRecord(e->join[i], c->stream);
+            if (err == cudaSuccess && rc == P3M_OK) err = cudaStreamWaitEvent(e->parent, e->join[i], 0);
+        }
+        for (int g = 0; g < e->ngrp && phase < 2 && err == cudaSuccess && rc == P3M_OK; ++g) {
+            FftGroup &G = e->grp[g];
+            const bool f32 = G.precision == P3M_PREC_MIXED;
+            const cufftResult r =
+                phase == 0 ? (f32 ? cufftExecR2C(G.r2c, (cufftReal *)G.rho, (cufftComplex *)G.rho_k)
+                                  : cufftExecD2Z(G.r2c, (cufftDoubleReal *)G.rho, (cufftDoubleComplex *)G.rho_k))
+                           : (f32 ? cufftExecC2R(G.c2r, (cufftComplex *)G.frc_k, (cufftReal *)G.frc)
+                                  : cufftExecZ2D(G.c2r, (cufftDoubleComplex *)G.frc_k, (cufftDoubleReal *)G.frc));
+            if (r != CUFFT_SUCCESS) return p3m_fail_global(P3M_ECUFFT, "ensemble step: batched cuFFT code %d", (int)r);
+            e->launches += 1;
+        }
+    }
+    if (rc != P3M_OK) {
+        for (int i = 0; i < e->n; ++i)
+            if (e->c[i]->err[0] && strcmp(e->c[i]->err, "no error")) return p3m_fail_global(rc, "ensemble step: %s", e->c[i]->err);
+        return p3m_fail_global(rc, "ensemble step failed");
+    }
+    if (err != cudaSuccess)
+        return p3m_fail_global(P3M_ECUDA, "ensemble step: %s", cudaGetErrorString(err));
+    return P3M_OK;
+}
+
+// Point every grouped context back at its own meshes (copying the group slices' contents there)
+// and release the groups' buffers and plans.
+void ungroup(p3m_ensemble *e)
+{
+    if (e->parent) cudaStreamSynchronize(e->parent);
+    for (int i = 0; i < e->n && e->gi; ++i) {
+        const int g = e->gi[i];
+        if (g < 0) continue;
+        p3m_ctx *c = e->c[i];
+        FftGroup &G = e->grp[g];
+        cudaStreamSynchronize(c->stream);
+        void **own = e->saved + 4 * i;
+        cudaMemcpy(own[0], c->rho, G.rho_b, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(own[1], c->rho_k, G.rhok_b, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(own[2], c->frc_k, G.frck_b, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(own[3], c->frc, G.frc_b, cudaMemcpyDeviceToDevice);
+        c->rho = own[0];
+        c->rho_k = own[1];
+        c->frc_k = own[2];
+        c->frc = own[3];
+        ++c->geom_version;  // graphs that baked the slices go stale
+        e->gi[i] = -1;
+    }
+    for (int g = 0; g < e->ngrp; ++g) {
+        FftGroup &G = e->grp[g];
+        if (G.plans) {
+            cufftDestroy(G.r2c);
+            cufftDestroy(G.c2r);
+        }
+        void *bufs[] = {G.rho, G.rho_k, G.frc_k, G.frc};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+    }
+    free(e->grp);
+    e->grp = nullptr;
+    e->ngrp = 0;
+    e->grouped = false;
+}
+
+// Groups the contexts by (mesh, precision); every group of at least two gets one allocation
+// per mesh buffer, sliced among its members, and batched plans on the parent stream.
+int group_ffts(p3m_ensemble *e)
+{
+    std::vector<int> key(e->n, -1);
+    std::vector<FftGroup> gs;
+    std::vector<std::vector<int>> members;
+    for (int i = 0; i < e->n; ++i) {
+        p3m_ctx *c = e->c[i];
+        int g = -1;
+        for (size_t k = 0; k < gs.size() && g < 0; ++k)
+            if (gs[k].mesh == c->g.mesh && gs[k].precision == c->precision) g = (int)k;
+        if (g < 0) {
+            FftGroup G;
+            memset(&G, 0, sizeof(G));
+            G.mesh = c->g.mesh;
+            G.precision = c->precision;
+            gs.push_back(G);
+            members.emplace_back();
+            g = (int)gs.size() - 1;
+        }
+        members[g].push_back(i);
+    }
+    e->grp = (FftGroup *)calloc(gs.size() ? gs.size() : 1, sizeof(FftGroup));
+    if (!e->grp) return P3M_ENOMEM;
+    for (int i = 0; i < e->n; ++i) e->gi[i] = -1;
+    for (size_t k = 0; k < gs.size(); ++k) {
+        if (members[k].size() < 2) continue;
+        FftGroup &G = e->grp[e->ngrp];
+        G = gs[k];
+        G.count = (int)members[k].size();
+        const size_t M = (size_t)G.mesh, M3 = M * M * M, nk = M * M * (M / 2 + 1);
+        const size_t real = G.precision == P3M_PREC_MIXED ? 4 : 8;
+        G.rho_b = real * M3;
+        G.rhok_b = 2 * real * nk;
+        G.frck_b = 6 * real * nk;
+        G.frc_b = 3 * real * M3;
+        cudaError_t err = cudaMalloc(&G.rho, G.rho_b * G.count);
+        if (err == cudaSuccess) err = cudaMalloc(&G.rho_k, G.rhok_b * G.count);
+        if (err == cudaSuccess) err = cudaMalloc(&G.frc_k, G.frck_b * G.count);
+        if (err == cudaSuccess) err = cudaMalloc(&G.frc, G.frc_b * G.count);
+        ++e->ngrp;  // (released by ungroup on failure)
+        if (err != cudaSuccess) return P3M_ENOMEM;
+        int dims[3] = {G.mesh, G.mesh, G.mesh};
+        const bool f32 = G.precision == P3M_PREC_MIXED;
+        cufftResult r = cufftPlanMany(&G.r2c, 3, dims, nullptr, 1, (int)M3, nullptr, 1, (int)nk,
+                                      f32 ? CUFFT_R2C : CUFFT_D2Z, G.count);
+        if (r == CUFFT_SUCCESS) {
+            r = cufftPlanMany(&G.c2r, 3, dims, nullptr, 1, (int)nk, nullptr, 1, (int)M3,
+                              f32 ? CUFFT_C2R : CUFFT_Z2D, 3 * G.count);
+            if (r != CUFFT_SUCCESS) cufftDestroy(G.r2c);
+        }
+        if (r != CUFFT_SUCCESS) return P3M_ECUFFT;
+        G.plans = true;
+        cufftSetStream(G.r2c, e->parent);
+        cufftSetStream(G.c2r, e->parent);
+        for (int s_ = 0; s_ < G.count; ++s_) {
+            const int i = members[k][s_];
+            p3m_ctx *c = e->c[i];
+            CK(cudaStreamSynchronize(c->stream));
+            void **own = e->saved + 4 * i;
+            own[0] = c->rho;
+            own[1] = c->rho_k;
+            own[2] = c->frc_k;
+            own[3] = c->frc;
+            c->rho = (char *)G.rho + G.rho_b * s_;
+            c->rho_k = (char *)G.rho_k + G.rhok_b * s_;
+            c->frc_k = (char *)G.frc_k + G.frck_b * s_;
+            c->frc = (char *)G.frc + G.frc_b * s_;
+            ++c->geom_version;
+            e->gi[i] = e->ngrp - 1;
+        }
+    }
+    e->grouped = e->ngrp > 0;
     return P3M_OK;
 }
 
@@ -239,11 +430,42 @@ extern "C" int p3m_ensemble_create(p3m_ensemble **out, p3m_ctx *const *ctxs, int
     }
     e->batched = false;  // within 1 % of per-context branches on an uneven ensemble, which
                          // keep the contexts independent
+    // size-grouped FFTs, on by default when some group has at least two contexts
+    e->gi = (int *)malloc(sizeof(int) * n);
+    e->saved = (void **)calloc(4 * (size_t)n, sizeof(void *));
+    e->k2 = (double *)calloc(n, sizeof(double));
+    if (err == cudaSuccess && (!e->gi || !e->saved || !e->k2)) err = cudaErrorMemoryAllocation;
+    if (err == cudaSuccess) {
+        const int rc = group_ffts(e);
+        if (rc != P3M_OK) {
+            ungroup(e);
+            p3m_ensemble_free(e);
+            return p3m_fail_global(rc, "p3m_ensemble_create: grouping the FFTs failed");
+        }
+    }
     if (err != cudaSuccess) {
         p3m_ensemble_free(e);
         return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_create: %s", cudaGetErrorString(err));
     }
     *out = e;
+    return P3M_OK;
+}
+
+extern "C" int p3m_ensemble_set_fft_groups(p3m_ensemble *e, int enable)
+{
+    if (!e) return p3m_fail_global(P3M_EINVAL, "p3m_ensemble_set_fft_groups: NULL ensemble");
+    const bool want = enable != 0;
+    if (want == (e->grp != nullptr)) return P3M_OK;
+    drop_graphs(e);
+    if (!want) {
+        ungroup(e);
+        return P3M_OK;
+    }
+    const int rc = group_ffts(e);
+    if (rc != P3M_OK) {
+        ungroup(e);
+        return p3m_fail_global(rc, "p3m_ensemble_set_fft_groups: grouping the FFTs failed");
+    }
     return P3M_OK;
 }
 
@@ -283,6 +505,16 @@ extern "C" int p3m_ensemble_run(p3m_ensemble *e, const double *a_list, int n_ste
             if (rc) return rc;
         }
         // later work on the contexts' own streams comes after the last batched launch
+        cudaError_t err = cudaEventRecord(e->fork, e->parent);
+        for (int i = 0; i < e->n && err == cudaSuccess; ++i)
+            err = cudaStreamWaitEvent(e->c[i]->stream, e->fork, 0);
+        if (err != cudaSuccess)
+            return p3m_fail_global(P3M_ECUDA, "p3m_ensemble_run: %s", cudaGetErrorString(err));
+    } else if (!use_graph && e->grouped) {
+        for (int k = 0; k < n_steps; ++k) {
+            int rc = ens_step_fft(e, a_list[k], a_list[k + 1] - a_list[k], false);
+            if (rc) return rc;
+        }
         cudaError_t err = cudaEventRecord(e->fork, e->parent);
         for (int i = 0; i < e->n && err == cudaSuccess; ++i)
             err = cudaStreamWaitEvent(e->c[i]->stream, e->fork, 0);
@@ -378,6 +610,10 @@ extern "C" void p3m_ensemble_free(p3m_ensemble *e)
     if (!e) return;
     if (e->parent) cudaStreamSynchronize(e->parent);
     drop_graphs(e);
+    if (e->grp) ungroup(e);
+    free(e->gi);
+    free(e->saved);
+    free(e->k2);
     for (int i = 0; i < e->n; ++i) {
         if (e->c && e->c[i] && e->own && e->own[i]) {
             p3m_set_stream(e->c[i], nullptr);

@@ -58,6 +58,17 @@ int check_flags(p3m_ctx *c);
 // Sort by cell, mesh force, pair force at the current (keyed) positions; see api.cu.
 int evaluate(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table = false,
              bool pairs = true);
+// The phases of evaluate, in order: sort, permute and deposit; R2C; k-space pass; C2R; gather
+// and pair force (with the fused kick).
+int eval_pre(p3m_ctx *c);
+int eval_r2c(p3m_ctx *c);
+int eval_kspace(p3m_ctx *c);
+int eval_c2r(p3m_ctx *c);
+int eval_post(p3m_ctx *c, double kfac, double *sr_only_out, bool from_table, bool pairs);
+// The parts of step_body: factors, first half kick and drift (second kick's factor in *k2), and
+// the energy bookkeeping after the forces.
+int step_kd(p3m_ctx *c, double a, double da, bool from_table, double *k2);
+int step_tail(p3m_ctx *c, double a, double da, bool from_table);
 // Wrap and key the current positions (no kick, no drift).
 int key_current(p3m_ctx *c);
 bool finite_pos(double x);

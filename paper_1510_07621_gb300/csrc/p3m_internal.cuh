@@ -86,9 +86,9 @@ struct p3m_ctx {
     double *ps_acc;                // power spectrum sums (3 * (M/2) + 1)
     double *ps_part;               // power spectrum per-block partial sums (ps_blocks rows)
     int ps_blocks;
-    // fixed-point deposit accumulator: 3 M^3 64-bit integers, all zero between deposits (each
-    // conversion pass clears what it read); sums of integers do not depend on the order of the
-    // atomic additions, so every run gives the same mesh
+    // fixed-point deposit accumulator: 3 M^3 64-bit integers, cleared before each deposit; sums
+    // of integers do not depend on the order of the atomic additions, so every run gives the
+    // same mesh
     unsigned long long *rho_fix;
     int *fix_exp;  // scale exponent of the vector deposit (set on the device)
     double green_const;

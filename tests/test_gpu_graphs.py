@@ -57,9 +57,11 @@ def test_graph_steps_follow_host_steps(mod, precision):
     assert abs(d["a"] - a[-1]) < 1e-15
 
 
-def test_ensemble_matches_individual_runs(mod):
-    """FP64 ensembles, graph-replayed and host-issued: every member's trajectory equals its
-    individual run bit for bit."""
+@pytest.mark.parametrize("fft_groups", [True, False])
+def test_ensemble_matches_individual_runs(mod, fft_groups):
+    """FP64 ensembles, graph-replayed and host-issued, with the FFTs batched per mesh size (two
+    of the three members share mesh 32) or per member: every member's trajectory equals its
+    individual run bit for bit, and so do its meshes after the ensemble is freed."""
     torch, m = mod
     specs = [(16, 32.0, 32, 11), (24, 40.0, 24, 12), (32, 64.0, 32, 13)]
     a = S.log_spaced_steps(0.05, 0.2, 12)
@@ -76,12 +78,15 @@ def test_ensemble_matches_individual_runs(mod):
                 for n_p, box, mesh, seed in specs]
         for s_, (pos, mom) in zip(sims, ics):
             s_.set_particles(pos, mom, a=a[0])
-        with m.Ensemble(sims) as ens:
+        with m.Ensemble(sims, fft_groups=fft_groups) as ens:
             ens.run(a[:3], use_graph=use_graph)   # 2 single-step graphs
             ens.run(a[2:], use_graph=use_graph)   # one 8-step chunk graph, then 2 single steps
-        for s_, (n_p, box, mesh, seed), (rp, rm) in zip(sims, specs, refs):
+            torch.cuda.synchronize()
+            dens = [s_.get_mesh(1) for s_ in sims]
+        for s_, (n_p, box, mesh, seed), (rp, rm), dm in zip(sims, specs, refs, dens):
             gp, gm = s_.get_particles()
             assert np.array_equal(gp, rp) and np.array_equal(gm, rm), _max_dx(gp, rp, box)
+            assert np.array_equal(s_.get_mesh(1), dm)  # the group slices were copied back
             s_.close()
 
 
