@@ -302,7 +302,9 @@ def run_ours(args, rank, world, local_rank, dist):
         "kick_drift": 124 * n,
         "sort": 16 * passes * n,  # key histogram read (4 B), then per pass key + slot in and out
         "permute": 128 * n,
-        "deposit": 32 * n,
+        # relative coordinates and key (20 B per particle); per node: the accumulator cleared,
+        # accumulated once, read by the conversion (8 B each) and the FP32 mesh written (4 B)
+        "deposit": 20 * n + 28 * M ** 3,
         "kspace": 32 * nk,
         "gather": 60 * n,
     }
