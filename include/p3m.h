@@ -54,6 +54,8 @@ extern "C" {
 #define P3M_ESTATE (-5)     /* call out of order (e.g. a step before any particles)     */
 #define P3M_ETIMEOUT (-6)   /* a bounded device-side wait gave up (error flag was set)  */
 #define P3M_ENONFINITE (-7) /* NaN or Inf in the particle input                         */
+#define P3M_EBOUNDS (-8)    /* debug builds: a kernel's bounds check failed, or the guard
+                               bytes after an allocation were overwritten                  */
 
 /* precision modes */
 #define P3M_PREC_MIXED 0 /* FP32 mesh, FFTs and pair forces; FP64 positions, momenta and
@@ -413,6 +415,21 @@ int p3m_cell_sort_noalloc(const double *pos3n, int64_t n, double box, int n_c, i
 #define P3M_INJECT_FFT_PLAN 2
 #define P3M_INJECT_SORT_TIMEOUT 3
 int p3m_inject_fault(p3m_ctx *ctx, int what, int64_t arg);
+
+/*
+ * Checks of debug builds (the library compiled with -DP3M_DEBUG_CHECKS; the guide has no
+ * counterpart; they stand in for a memory checker).  In such a build the kernels test the
+ * indices they compute (mesh nodes of the deposit and gather, source slots of the permute, cell
+ * ranges, key range, pair tile lengths) and, on a failed test, set a flag and skip the access;
+ * and every device allocation of p3m_init is followed by 256 guard bytes of a fixed pattern.
+ * p3m_debug_check synchronises, reports a set flag or an overwritten guard byte as P3M_EBOUNDS
+ * (with the allocation's index in the message) and clears the flag; in release builds it checks
+ * the flags only.  p3m_debug_poke_canary overwrites one guard byte of allocation k (host-side,
+ * inside that allocation), so that a test can see the check catch it; P3M_ESTATE in release
+ * builds.
+ */
+int p3m_debug_check(p3m_ctx *ctx);
+int p3m_debug_poke_canary(p3m_ctx *ctx, int k);
 
 /* Message of the last failure on ctx (ctx NULL: the last failed p3m_init).  Never NULL. */
 const char *p3m_last_error(const p3m_ctx *ctx);

@@ -71,8 +71,8 @@ class P3M:
                  cutoff: float = 4.5, omega_m: float = 1.0, omega_lambda: float = 0.0,
                  h0: float = 100.0, precision: str = "mixed", softening: float = 0.02,
                  deconvolve: bool = True, short_range: bool = True, sub_bits: int = 3,
-                 stream=None):
-        lib = load()
+                 stream=None, lib=None):
+        lib = lib or load()
         self._lib = lib
         self.n = int(n)
         self.box = float(box)
@@ -98,7 +98,7 @@ class P3M:
         cos = Cosmology(float(omega_m), float(omega_lambda), float(h0))
         ctx = ctypes.c_void_p()
         check(lib.p3m_init(ctypes.byref(ctx), self.box, self.n, self.mesh, float(r_s_cells),
-                           float(cutoff), ctypes.byref(cos), ctypes.byref(opt)), None)
+                           float(cutoff), ctypes.byref(cos), ctypes.byref(opt)), None, lib)
         self._ctx = ctx
 
     # ------------------------------------------------------------------ lifetime
@@ -120,7 +120,7 @@ class P3M:
         self.close()
 
     def _check(self, code):
-        return check(code, self._ctx)
+        return check(code, self._ctx, self._lib)
 
     # ------------------------------------------------------------------ particles
     def set_particles(self, pos, mom, acc=None, mass: float = 1.0, a: float = 1.0):
@@ -299,23 +299,24 @@ class Ensemble:
 
     def __init__(self, sims, own_streams: bool = True, batched: bool | None = None,
                  fft_groups: bool | None = None):
-        self._lib = load()
+        self._lib = sims[0]._lib if sims else load()
         self.sims = list(sims)
         arr = (ctypes.c_void_p * len(self.sims))(*[s._ctx.value for s in self.sims])
         self._arr = arr
         e = ctypes.c_void_p()
         check(self._lib.p3m_ensemble_create(ctypes.byref(e), arr, len(self.sims),
-                                            1 if own_streams else 0), None)
+                                            1 if own_streams else 0), None, self._lib)
         self._e = e
         if batched is not None:  # None: the library's default (per-simulation pair launches)
-            check(self._lib.p3m_ensemble_set_batched(self._e, 1 if batched else 0), None)
+            check(self._lib.p3m_ensemble_set_batched(self._e, 1 if batched else 0), None, self._lib)
         if fft_groups is not None:  # None: the library's default (size-grouped batched FFTs)
-            check(self._lib.p3m_ensemble_set_fft_groups(self._e, 1 if fft_groups else 0), None)
+            check(self._lib.p3m_ensemble_set_fft_groups(self._e, 1 if fft_groups else 0), None,
+                  self._lib)
 
     def run(self, a_list, use_graph: bool = True):
         a = np.ascontiguousarray(a_list, dtype=np.float64)
         check(self._lib.p3m_ensemble_run(self._e, a.ctypes.data, len(a) - 1,
-                                         1 if use_graph else 0), None)
+                                         1 if use_graph else 0), None, self._lib)
 
     def close(self):
         if getattr(self, "_e", None) is not None and self._e.value:

@@ -20,6 +20,7 @@ P3M_ECUFFT = -4
 P3M_ESTATE = -5
 P3M_ETIMEOUT = -6
 P3M_ENONFINITE = -7
+P3M_EBOUNDS = -8
 P3M_PREC_MIXED = 0
 P3M_PREC_FP64 = 1
 P3M_NPHASES = 10
@@ -91,6 +92,8 @@ SIGNATURES = {
     "p3m_autotune": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _vp]),
     "p3m_get_tuning": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "p3m_inject_fault": (_c.c_int, [_vp, _c.c_int, _c.c_int64]),
+    "p3m_debug_check": (_c.c_int, [_vp]),
+    "p3m_debug_poke_canary": (_c.c_int, [_vp, _c.c_int]),
     "p3m_cell_sort_noalloc": (_c.c_int, [_vp, _c.c_int64, _c.c_double, _c.c_int, _c.c_int,
                                          _vp, _vp, _vp, _vp]),
     "p3m_measure_fma_peak": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_double)]),
@@ -101,22 +104,25 @@ SIGNATURES = {
 _lib = None
 
 
-def load(path: str | None = None):
-    """Loads libp3m.so (building it first is the caller's job: ``build.build()``)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    p = path or LIB_PATH
-    if not os.path.exists(p):
-        raise RuntimeError(f"{p} is missing: build it with paper_1510_07621_gb300.build.build() "
+def bind(path: str):
+    """Loads the library at ``path`` with the C ABI's signatures (not cached)."""
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1510_07621_gb300.build.build() "
                            "(the P3M path has no CPU fallback)")
-    lib = ctypes.CDLL(p)
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
+
+
+def load(path: str | None = None):
+    """Loads libp3m.so once (building it first is the caller's job: ``build.build()``)."""
+    global _lib
+    if _lib is None:
+        _lib = bind(path or LIB_PATH)
+    return _lib
 
 
 class P3MError(RuntimeError):
@@ -125,8 +131,8 @@ class P3MError(RuntimeError):
         self.code = code
 
 
-def check(code: int, ctx=None):
+def check(code: int, ctx=None, lib=None):
     if code != P3M_OK:
-        msg = load().p3m_last_error(ctx).decode(errors="replace")
+        msg = (lib or load()).p3m_last_error(ctx).decode(errors="replace")
         raise P3MError(code, msg)
     return code

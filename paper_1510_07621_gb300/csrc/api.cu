@@ -206,11 +206,30 @@ void release(p3m_ctx *c)
 int g_inject_alloc = -1;
 bool g_inject_fft = false;
 
+#ifdef P3M_DEBUG_CHECKS
+constexpr size_t kCanaryBytes = 256;  // guard bytes after each allocation of p3m_init
+constexpr unsigned char kCanary = 0xA5;
+#endif
+
 template <typename T>
-cudaError_t dalloc(T **p, size_t bytes)
+cudaError_t dalloc(T **p, size_t bytes, p3m_ctx *c)
 {
     *p = nullptr;
-    return cudaMalloc((void **)p, bytes < 16 ? 16 : bytes);
+    bytes = bytes < 16 ? 16 : bytes;
+#ifdef P3M_DEBUG_CHECKS
+    const size_t off = (bytes + 255) / 256 * 256;  // the guard starts 256-byte aligned
+    cudaError_t e = cudaMalloc((void **)p, off + kCanaryBytes);
+    if (e == cudaSuccess) e = cudaMemset((char *)*p + off, kCanary, kCanaryBytes);
+    if (e == cudaSuccess && c->n_canary < 64) {
+        c->canary_ptr[c->n_canary] = *p;
+        c->canary_off[c->n_canary] = off;
+        ++c->n_canary;
+    }
+    return e;
+#else
+    (void)c;
+    return cudaMalloc((void **)p, bytes);
+#endif
 }
 
 int check_flags(p3m_ctx *c)
@@ -218,6 +237,11 @@ int check_flags(p3m_ctx *c)
     uint32_t flags = 0;
     CK(cudaMemcpyAsync(&flags, c->counters + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (flags & P3M_FLAG_BOUNDS) {
+        CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(uint32_t), c->stream));
+        c->forces_valid = false;
+        return fail(c, P3M_EBOUNDS, "a debug bounds check failed in a kernel (the access was skipped)");
+    }
     if (flags & P3M_FLAG_TIMEOUT) {
         CK(cudaMemsetAsync(c->counters + 1, 0, sizeof(uint32_t), c->stream));  // reported once
         c->forces_valid = false;
@@ -602,7 +626,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         int idx = 0;
         for (auto &a : allocs) {
             const bool injected = idx++ == g_inject_alloc;
-            e = injected ? cudaErrorMemoryAllocation : dalloc(a.p, a.bytes);
+            e = injected ? cudaErrorMemoryAllocation : dalloc(a.p, a.bytes, c);
             if (e != cudaSuccess) {
                 rc = fail(nullptr, P3M_ENOMEM, "p3m_init: cudaMalloc of %zu bytes failed: %s%s", a.bytes,
                           cudaGetErrorString(e), injected ? " (injected)" : "");
@@ -610,6 +634,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
             }
         }
         if (rc != P3M_OK) break;
+        c->g.flags = c->counters + 1;
         cudaMemsetAsync(c->counters, 0, 16, c->stream);
         cudaMemsetAsync(c->pair_count, 0, 64, c->stream);
         // sort buffers start at zero: every key and slot they ever hold is then in range
@@ -734,6 +759,7 @@ const void *pinned_view(const void *p)
 extern "C" int p3m_set_particles(p3m_ctx *c, const double *pos, const double *mom,
                                  const double *acc, double mass, double a, int on_device)
 {
+    Range nvtx_range("p3m_set_particles");
     if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
     if (!pos || !mom) return fail(c, P3M_EINVAL, "p3m_set_particles: pos and mom are required");
     if (!finite_pos(mass)) return fail(c, P3M_EINVAL, "p3m_set_particles: mass must be > 0");
@@ -777,6 +803,7 @@ extern "C" int p3m_set_particles(p3m_ctx *c, const double *pos, const double *mo
 
 extern "C" int p3m_forces(p3m_ctx *c, double a, double *acc3n, int on_device)
 {
+    Range nvtx_range("p3m_forces");
     if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
     if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_forces: no particles loaded");
     if (!finite_pos(a)) return fail(c, P3M_EINVAL, "p3m_forces: a must be > 0");
@@ -818,6 +845,7 @@ extern "C" int p3m_forces_split(p3m_ctx *c, double *acc_lr, double *acc_sr, int 
 
 extern "C" int p3m_step(p3m_ctx *c, double a, double da)
 {
+    Range nvtx_range("p3m_step");
     if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
     if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_step: no particles loaded");
     if (!finite_pos(a) || !finite_pos(da)) return fail(c, P3M_EINVAL, "p3m_step: need a > 0, da > 0");
@@ -838,6 +866,7 @@ extern "C" int p3m_step(p3m_ctx *c, double a, double da)
 extern "C" int p3m_power_spectrum(p3m_ctx *c, int n_bins, int deconvolve, double tophat_radius,
                                   double *k_mean, double *power, double *n_modes, double *sigma)
 {
+    Range nvtx_range("p3m_power_spectrum");
     if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
     if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_power_spectrum: no particles loaded");
     const int nb_max = c->g.mesh / 2;
@@ -867,6 +896,7 @@ extern "C" int p3m_power_spectrum(p3m_ctx *c, int n_bins, int deconvolve, double
 
 extern "C" int p3m_get_particles(p3m_ctx *c, double *pos, double *mom, double *acc, int on_device)
 {
+    Range nvtx_range("p3m_get_particles");
     if (!c) return fail(c, P3M_EINVAL, "ctx is NULL");
     if (!c->have_particles) return fail(c, P3M_ESTATE, "p3m_get_particles: no particles loaded");
     if (acc && !c->forces_valid) return fail(c, P3M_ESTATE, "p3m_get_particles: forces not evaluated");
@@ -1051,4 +1081,37 @@ extern "C" int p3m_inject_fault(p3m_ctx *c, int what, int64_t arg)
     default:
         return fail(c, P3M_EINVAL, "p3m_inject_fault: unknown fault %d", what);
     }
+}
+
+extern "C" int p3m_debug_check(p3m_ctx *c)
+{
+    if (!c) return fail(c, P3M_EINVAL, "p3m_debug_check: ctx is NULL");
+    const int rc = check_flags(c);
+    if (rc) return rc;
+#ifdef P3M_DEBUG_CHECKS
+    unsigned char guard[kCanaryBytes];
+    for (int k = 0; k < c->n_canary; ++k) {
+        CK(cudaMemcpy(guard, (const char *)c->canary_ptr[k] + c->canary_off[k], kCanaryBytes,
+                      cudaMemcpyDeviceToHost));
+        for (size_t b = 0; b < kCanaryBytes; ++b)
+            if (guard[b] != kCanary)
+                return fail(c, P3M_EBOUNDS, "p3m_debug_check: guard bytes after allocation %d were "
+                            "overwritten (byte %zu)", k, b);
+    }
+#endif
+    return P3M_OK;
+}
+
+extern "C" int p3m_debug_poke_canary(p3m_ctx *c, int k)
+{
+    if (!c) return fail(c, P3M_EINVAL, "p3m_debug_poke_canary: ctx is NULL");
+#ifdef P3M_DEBUG_CHECKS
+    if (k < 0 || k >= c->n_canary) return fail(c, P3M_EINVAL, "p3m_debug_poke_canary: no allocation %d", k);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemset((char *)c->canary_ptr[k] + c->canary_off[k] + 17, 0, 1));
+    return P3M_OK;
+#else
+    (void)k;
+    return fail(c, P3M_ESTATE, "p3m_debug_poke_canary: not a debug build (P3M_DEBUG_CHECKS)");
+#endif
 }

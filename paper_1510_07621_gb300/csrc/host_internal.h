@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include "p3m_internal.cuh"
@@ -30,12 +31,16 @@ namespace p3m_host {
 // Writes the message into c->err (or the global message when c is NULL); returns code.
 int fail(p3m_ctx *c, int code, const char *fmt, ...);
 
-// CUDA-event timing of one phase on the context's stream (skipped while capturing a graph).
+extern const char *kPhaseNames[P3M_NPHASES];
+
+// One phase on the context's stream: an NVTX range named after the phase (host-side, for
+// profilers' timelines), and CUDA-event timing when enabled (skipped while capturing a graph).
 struct Phase {
     p3m_ctx *c;
     int id;
     Phase(p3m_ctx *c_, int id_) : c(c_), id(id_)
     {
+        nvtxRangePushA(kPhaseNames[id_]);
         if (c->timing && !c->capturing && c->ev_used + 2 <= c->ev_cap) {
             cudaEventRecord(c->ev[c->ev_used], c->stream);
             c->ev_phase[c->ev_used] = id;
@@ -50,7 +55,14 @@ struct Phase {
             c->ev_phase[c->ev_used + 1] = id;
             c->ev_used += 2;
         }
+        nvtxRangePop();
     }
+};
+
+// An NVTX range over one call of the C ABI.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
 };
 
 // Reads the device flags (a bounded wait that gave up); synchronises.

@@ -193,7 +193,9 @@ __global__ void __launch_bounds__(256)
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    unsigned long long *row = tile + ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
+                    const long long t = ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
+                    if (!p3m_in_bounds(t >= 0 && t + 1 < vol, g.flags)) continue;
+                    unsigned long long *row = tile + t;
                     atomicAdd(row, to_fixed(w[(a << 2) | (b << 1)], scale));
                     atomicAdd(row + 1, to_fixed(w[(a << 2) | (b << 1) | 1], scale));
                 }
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(256)
                 const int lz = t % bdim[2], ly = (t / bdim[2]) % bdim[1], lx = t / (bdim[2] * bdim[1]);
                 const size_t node = ((size_t)wrap_index(blo[0] + lx, M) * M + wrap_index(blo[1] + ly, M)) * M +
                                     wrap_index(blo[2] + lz, M);
-                atomicAdd(fix + node, v);
+                if (p3m_in_bounds(node < (size_t)M * M * M, g.flags)) atomicAdd(fix + node, v);
             }
         }
     } else {
@@ -222,7 +224,8 @@ __global__ void __launch_bounds__(256)
                     for (int c = 0; c < 2; ++c) {
                         const size_t node = ((size_t)wrap_index(i0[r][0] + a, M) * M +
                                              wrap_index(i0[r][1] + b, M)) * M + wrap_index(i0[r][2] + c, M);
-                        atomicAdd(fix + node, to_fixed(wx[a] * wy[b] * wz[c], scale));
+                        if (p3m_in_bounds(node < (size_t)M * M * M, g.flags))
+                            atomicAdd(fix + node, to_fixed(wx[a] * wy[b] * wz[c], scale));
                     }
         }
     }
@@ -321,6 +324,7 @@ __global__ void __launch_bounds__(256)
                 for (int c = 0; c < 2; ++c) {
                     const float w = wx[a] * wy[b] * wz[c];
                     const size_t node = ((size_t)jx[a] * M + jy[b]) * M + jz[c];
+                    if (!p3m_in_bounds(node < (size_t)M * M * M, g.flags)) continue;
                     ax += w * __ldg(fxm + node);
                     ay += w * __ldg(fym + node);
                     az += w * __ldg(fzm + node);
@@ -357,6 +361,7 @@ __global__ void __launch_bounds__(256)
                 for (int c = 0; c < 2; ++c) {
                     const double w = wx[a] * wy[b] * wz[c];
                     const size_t node = ((size_t)jx[a] * M + jy[b]) * M + jz[c];
+                    if (!p3m_in_bounds(node < (size_t)M * M * M, g.flags)) continue;
                     ax += w * __ldg(fxm + node);
                     ay += w * __ldg(fym + node);
                     az += w * __ldg(fzm + node);

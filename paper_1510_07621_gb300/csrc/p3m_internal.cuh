@@ -33,7 +33,23 @@ struct P3MGeom {
     double cs;        // L / n_c
     int n_cells;      // n_c^3
     double mean_count;  // N / M^3
+    uint32_t *flags;    // the context's device error flags (debug bounds checks record here)
 };
+
+// Bounds checks of debug builds (compiled with -DP3M_DEBUG_CHECKS): p3m_in_bounds(ok, flags)
+// records a failed check in the context's flags (P3M_FLAG_BOUNDS) and returns ok, so that the
+// caller skips the access; nothing traps.  In release builds it is the constant true and the
+// check disappears.
+#define P3M_FLAG_BOUNDS 4u
+#ifdef P3M_DEBUG_CHECKS
+__device__ __forceinline__ bool p3m_in_bounds(bool ok, uint32_t *flags)
+{
+    if (!ok && flags) atomicOr(flags, P3M_FLAG_BOUNDS);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool p3m_in_bounds(bool, uint32_t *) { return true; }
+#endif
 
 struct p3m_ctx {
     P3MGeom g;
@@ -131,6 +147,11 @@ struct p3m_ctx {
     bool track_energy;
     double li_a0, li_e0;
 
+    // debug builds: the guard bytes after every device allocation of p3m_init (canaries)
+    int n_canary;
+    void *canary_ptr[64];
+    size_t canary_off[64];
+
     bool have_particles;
     bool forces_valid;
     bool sorted_valid;
@@ -200,6 +221,7 @@ __device__ __forceinline__ NeighbourF make_neighbour(const P3MGeom &g, const uin
     NeighbourF r;
     r.start = cell_start[q];
     r.end = cell_start[q + 1];
+    if (!p3m_in_bounds(r.start <= r.end && r.end <= (uint32_t)g.n, g.flags)) r.end = r.start;
     if (r.start == r.end) r.start = r.end = 0;
     const double L = g.box, cs = g.cs;
     const double imx = ux < 0 ? -L : (ux >= nc ? L : 0.0);

@@ -125,7 +125,9 @@ __global__ void k_kick_drift_keys(double *__restrict__ pos, double *__restrict__
             pos[d * n + i] = x;
             f[d] = fine_index_fast(x, g.inv_fine, inv_f, tol, g.n_fine);
         }
-        keys[i] = make_key(f[0], f[1], f[2], g);
+        const uint32_t key = make_key(f[0], f[1], f[2], g);
+        p3m_in_bounds((key >> (3 * g.sub_bits)) < (uint32_t)g.n_cells, g.flags);
+        keys[i] = key;
     }
 }
 
@@ -491,7 +493,9 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
          blk += nwarps) {
         const int64_t k = blk * 32 + lane;
         const bool active = k < n;
-        const uint32_t j = min(perm[active ? k : blk * 32], (uint32_t)(n - 1));  // in bounds always
+        const uint32_t pj = perm[active ? k : blk * 32];
+        p3m_in_bounds(pj < (uint32_t)n, g.flags);
+        const uint32_t j = min(pj, (uint32_t)(n - 1));  // in bounds always
         const double x = pos[j], y = pos[n + j], z = pos[2 * n + j];
         R4 rv = make_rel<R4>(0.0, 0.0, 0.0);
         if (active) {
@@ -541,6 +545,7 @@ __global__ void k_cell_start(const uint32_t *__restrict__ keys, P3MGeom g,
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t prev = k > 0 ? (int64_t)(keys[k - 1] >> sh) : -1;
         const int64_t cur = k < n ? (int64_t)(keys[k] >> sh) : (int64_t)g.n_cells;
+        if (!p3m_in_bounds(cur <= (int64_t)g.n_cells, g.flags)) continue;
         for (int64_t c = prev + 1; c <= cur; ++c) cell_start[c] = (uint32_t)k;
     }
 }
