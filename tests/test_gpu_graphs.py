@@ -171,3 +171,38 @@ def test_repeated_runs_are_bit_identical(mod, precision):
             out.append((acc, p, q, rho, ps[1], ps[3]))
     for x, y in zip(out[0], out[1]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_fft_groups_toggle_and_energy_tracking(mod):
+    """FP32 ensemble of five members (a group of three at mesh 32, a group of two at mesh 24)
+    that track the Layzer-Irvine energy: runs with the FFTs batched per group, then per member
+    (groups turned off), then grouped again; every member's positions, momenta and energy
+    residual equal those of its individual run bit for bit."""
+    torch, m = mod
+    specs = [(16, 32.0, 32, 41), (16, 32.0, 32, 42), (24, 40.0, 24, 43), (16, 32.0, 32, 44),
+             (24, 40.0, 24, 45)]
+    a = S.log_spaced_steps(0.05, 0.15, 9)
+    ics = [S.zeldovich(n_p, box, a[0], seed) for n_p, box, mesh, seed in specs]
+    refs = []
+    for (n_p, box, mesh, seed), (pos, mom) in zip(specs, ics):
+        with m.P3M(box, n_p ** 3, mesh, stream=0) as r:
+            r.set_particles(pos, mom, a=a[0])
+            r.track_energy(True)
+            for k in range(9):
+                r.step(a[k], a[k + 1] - a[k])
+            refs.append(r.get_particles() + (r.diagnostics()["layzer_irvine"],))
+    sims = [m.P3M(box, n_p ** 3, mesh, stream=0) for n_p, box, mesh, seed in specs]
+    for s_, (pos, mom) in zip(sims, ics):
+        s_.set_particles(pos, mom, a=a[0])
+        s_.track_energy(True)
+    with m.Ensemble(sims) as ens:
+        ens.run(a[:4], use_graph=True)      # grouped (the default)
+        ens._lib.p3m_ensemble_set_fft_groups(ens._e, 0)
+        ens.run(a[3:7], use_graph=True)     # per-member FFTs
+        ens._lib.p3m_ensemble_set_fft_groups(ens._e, 1)
+        ens.run(a[6:], use_graph=False)     # grouped again, host-issued
+    for s_, (rp, rm, rli) in zip(sims, refs):
+        gp, gm = s_.get_particles()
+        assert np.array_equal(gp, rp) and np.array_equal(gm, rm)
+        assert s_.diagnostics()["layzer_irvine"] == rli
+        s_.close()
