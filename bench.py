@@ -744,23 +744,35 @@ def other_configs(args):
     this process after the main workload (N = 1, rank 0): their key figures for the default
     benchmark line."""
     import torch
+
+    def z512():
+        z = run_zeldovich512(args)
+        r = {k: z[k] for k in ("value", "unit", "ms_per_step", "force_evaluation_ms", "roofline",
+                               "pairs_per_step", "gpu_launches")}
+        r["workload"] = z["config"]["workload"]
+        r["phase_ms_per_evaluation"] = {k: v / 11 for k, v in z["phase_ms_total"].items()}
+        return r
+
+    def ens48():
+        e = run_ensemble(args)
+        return {"value": e["value"], "unit": e["unit"], "workload": e["config"]["workload"],
+                "modes": e["modes"], "speedup_graph_over_serial": e["speedup_graph_over_serial"]}
+
+    def adj128():
+        d = run_adjoint(args)
+        r = {k: d[k] for k in ("value", "unit", "forward_ms_per_step", "adjoint_ms_per_step",
+                               "adjoint_over_forward", "loss")}
+        r["workload"] = d["config"]["workload"]
+        return r
+
     out = {}
-    z = run_zeldovich512(args)
-    out["zeldovich512"] = {k: z[k] for k in ("value", "unit", "ms_per_step", "force_evaluation_ms",
-                                             "roofline", "pairs_per_step", "gpu_launches")}
-    out["zeldovich512"]["workload"] = z["config"]["workload"]
-    out["zeldovich512"]["phase_ms_per_evaluation"] = {k: v / 11 for k, v in z["phase_ms_total"].items()}
-    torch.cuda.empty_cache()
-    e = run_ensemble(args)
-    out["ensemble48"] = {"value": e["value"], "unit": e["unit"], "workload": e["config"]["workload"],
-                         "modes": e["modes"],
-                         "speedup_graph_over_serial": e["speedup_graph_over_serial"]}
-    torch.cuda.empty_cache()
-    d = run_adjoint(args)
-    out["adjoint128"] = {k: d[k] for k in ("value", "unit", "forward_ms_per_step",
-                                           "adjoint_ms_per_step", "adjoint_over_forward", "loss")}
-    out["adjoint128"]["workload"] = d["config"]["workload"]
-    torch.cuda.empty_cache()
+    for name, fn in (("zeldovich512", z512), ("ensemble48", ens48), ("adjoint128", adj128)):
+        try:  # one configuration failing (e.g. memory taken by another process) keeps the line
+            out[name] = fn()
+        except Exception as exc:  # noqa: BLE001 - reported in the line instead
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
     return out
 
 

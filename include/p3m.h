@@ -211,8 +211,8 @@ int p3m_set_stream(p3m_ctx *ctx, void *stream);
  * step parity), so each step of the whole ensemble is one graph launch; with use_graph = 0
  * the host issues every kernel of every context, context after context.  own_streams != 0
  * gives each context a stream of its own (p3m_ensemble_free returns them to the legacy
- * stream).  The ensemble borrows the contexts; free it before them.  Errors are reported
- * through p3m_last_error(NULL).
+ * stream).  The ensemble borrows the contexts; free it before them.  A context belongs to at
+ * most one ensemble at a time.  Errors are reported through p3m_last_error(NULL).
  */
 typedef struct p3m_ensemble p3m_ensemble;
 int p3m_ensemble_create(p3m_ensemble **ens, p3m_ctx *const *ctxs, int n_ctx, int own_streams);
