@@ -211,8 +211,8 @@ int p3m_set_stream(p3m_ctx *ctx, void *stream);
  * step parity), so each step of the whole ensemble is one graph launch; with use_graph = 0
  * the host issues every kernel of every context, context after context.  own_streams != 0
  * gives each context a stream of its own (p3m_ensemble_free returns them to the legacy
- * stream).  The ensemble borrows the contexts; free it before them.  A context belongs to at
- * most one ensemble at a time.  Errors are reported through p3m_last_error(NULL).
+ * stream).  The ensemble borrows the contexts; free it before them.  Errors are reported
+ * through p3m_last_error(NULL).
  */
 typedef struct p3m_ensemble p3m_ensemble;
 int p3m_ensemble_create(p3m_ensemble **ens, p3m_ctx *const *ctxs, int n_ctx, int own_streams);
@@ -238,7 +238,8 @@ int p3m_ensemble_set_batched(p3m_ensemble *ens, int enable);
  * deposit of all, the batched R2C, the k-space pass of all, the batched C2R, the gather and pair
  * force of all); without groups each context's steps are one independent branch.  Results equal
  * the per-context FFTs bit for bit.  p3m_ensemble_free (or enable = 0) copies the slices' contents
- * back into the contexts' own meshes and releases the group buffers.  Batched pair launches
+ * back into the contexts' own meshes and releases the group buffers.  A context already grouped
+ * by another ensemble keeps its own FFTs in this one.  Batched pair launches
  * (p3m_ensemble_set_batched) take precedence: with them on, each context runs its own FFTs.
  */
 int p3m_ensemble_set_fft_groups(p3m_ensemble *ens, int enable);

@@ -249,6 +249,7 @@ void ungroup(p3m_ensemble *e)
         c->rho_k = own[1];
         c->frc_k = own[2];
         c->frc = own[3];
+        c->fft_grouped = false;
         ++c->geom_version;  // graphs that baked the slices go stale
         e->gi[i] = -1;
     }
@@ -277,6 +278,7 @@ int group_ffts(p3m_ensemble *e)
     std::vector<std::vector<int>> members;
     for (int i = 0; i < e->n; ++i) {
         p3m_ctx *c = e->c[i];
+        if (c->fft_grouped) continue;  // already in another ensemble's group: keeps its FFTs
         int g = -1;
         for (size_t k = 0; k < gs.size() && g < 0; ++k)
             if (gs[k].mesh == c->g.mesh && gs[k].precision == c->precision) g = (int)k;
@@ -338,6 +340,7 @@ int group_ffts(p3m_ensemble *e)
             c->frc_k = (char *)G.frc_k + G.frck_b * s_;
             c->frc = (char *)G.frc + G.frc_b * s_;
             ++c->geom_version;
+            c->fft_grouped = true;
             e->gi[i] = e->ngrp - 1;
         }
     }

@@ -152,6 +152,8 @@ struct p3m_ctx {
     void *canary_ptr[64];
     size_t canary_off[64];
 
+    bool fft_grouped;  // its meshes are slices of an ensemble's FFT group (p3m_ensemble_set_fft_groups)
+
     bool have_particles;
     bool forces_valid;
     bool sorted_valid;
