@@ -692,7 +692,8 @@ def run_zeldovich512(args):
     pos, mom = S.zeldovich(n_p, box, 0.5, 1513)
     a = S.log_spaced_steps(0.5, 1.0, 10)
     out = {}
-    with P3M(box, n, n_p, softening=0.02, stream=stream) as sim:
+    extra = {} if args.sub_bits is None else {"sub_bits": args.sub_bits}
+    with P3M(box, n, n_p, softening=0.02, stream=stream, **extra) as sim:
         dpos = torch.from_numpy(pos).cuda()
         dmom = torch.from_numpy(mom).cuda()
         del pos, mom

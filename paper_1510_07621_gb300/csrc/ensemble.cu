@@ -273,7 +273,6 @@ void ungroup(p3m_ensemble *e)
 // per mesh buffer, sliced among its members, and batched plans on the parent stream.
 int group_ffts(p3m_ensemble *e)
 {
-    std::vector<int> key(e->n, -1);
     std::vector<FftGroup> gs;
     std::vector<std::vector<int>> members;
     for (int i = 0; i < e->n; ++i) {

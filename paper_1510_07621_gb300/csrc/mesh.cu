@@ -76,10 +76,11 @@ __device__ __forceinline__ unsigned long long to_fixed<double>(double w, double 
 // tile spanning the chunk's node bounding box (found by a block reduction); the tile is then
 // added to the mesh with one global atomic per non-zero node.  That pays for dense chunks (more
 // particles than box nodes); a sparse chunk, whose box holds more nodes than it has particles,
-// adds its 8 weights per particle straight to the mesh (measured: 10-18 % faster deposits on
-// clustered and near-uniform states than tiles for every chunk), as does a chunk whose box
-// exceeds the tile capacity (e.g. one that straddles the periodic boundary).  All sums are
-// 64-bit fixed-point integers (to_fixed).
+// adds its 8 weights per particle straight to the mesh, as does a chunk whose box exceeds the
+// tile capacity (e.g. one that straddles the periodic boundary).  All sums are 64-bit
+// fixed-point integers (to_fixed); with them, tiles for every chunk that fits made the deposit
+// 28 % slower on the evolved 128^3 state and 42 % slower at 256^3 (64-bit shared-memory atomics
+// cost more than the global reductions they save).
 constexpr int kDepChunk = 512;
 constexpr int kDepTileMax = 4096;  // nodes
 
