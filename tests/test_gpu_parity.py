@@ -368,3 +368,24 @@ def test_pinned_host_arrays_match_pageable_ones(P3M):
                 res.append((op, om, oa))
     for x, y in zip(res[0], res[1]):
         assert np.max(np.abs(x - y)) <= 1e-12 * max(1.0, np.max(np.abs(x)))
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-6), ("fp64", 1e-13)])
+def test_single_particle_feels_no_force(P3M, precision, tol):
+    """N = 1, the smallest input: no pairs, and the mesh force on a lone particle vanishes (the
+    CIC assignment and interpolation kernels are the same and the Green's function and the
+    gradient are symmetric), at an arbitrary position; a step moves it by its momentum only."""
+    box = 32.0
+    pos = np.array([[3.7], [20.25], [31.9]])
+    mom = np.array([[0.01], [-0.02], [0.005]])
+    with P3M(box, 1, 32, precision=precision) as sim:
+        sim.set_particles(pos, mom, a=0.5)
+        acc = sim.forces(0.5)
+        scale = 3.0 * box ** 3 / (8.0 * math.pi) / (box / 32) ** 2  # G m / h^2
+        assert np.max(np.abs(acc)) <= tol * scale
+        assert sim.diagnostics()["pairs"] == 0
+        k1, dfac, _ = sim.step_factors(0.5, 0.1)
+        sim.step(0.5, 0.1)
+        p, m = sim.get_particles()
+    dx = p - (pos + (mom + k1 * acc) * dfac)  # the half kick by the (vanishing) force, the drift
+    assert np.max(np.abs(dx)) <= 1e-12 * box
