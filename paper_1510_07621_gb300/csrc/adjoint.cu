@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(32)
 
 // FP32 mode: the force kernel's traversal and arithmetic style (one-warp persistent CTAs,
 // bulk-copy tiles of the block-SoA coordinates and v, block culling, the all-inside fast path,
-// two j particles per lane in packed f32x2, FP32 TwoSum accumulation), for
+// two j particles per lane in packed f32x2, per-tile FP32 sums added in FP64), for
 //   out_k += Gm sum_j [h(r) w + (h'(r)/r)(d.w) d],  w = v_j - v_k,
 //   h = g s^3, h'/r = -(r e / (2 sqrt(pi) r_s^3)) s^3 - 3 h s^2,  s = (r^2 + eps^2)^-1/2,
 //   e = exp(-r^2 / (4 r_s^2)),
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(32, 32)
         const float *vi = vfx + (ii >> 5) * kBlockFloats + (ii & 31);
         const f2 vix2 = f2_pack(vi[0], vi[0]), viy2 = f2_pack(vi[32], vi[32]),
                  viz2 = f2_pack(vi[64], vi[64]);
-        float sox = 0.0f, soy = 0.0f, soz = 0.0f, cox = 0.0f, coy = 0.0f, coz = 0.0f;
+        double sox = 0.0, soy = 0.0, soz = 0.0;
 
         auto next_tile = [&](int &nb, uint32_t &b) {
             while (nb < 27 && b * 32u >= nbr[nb].end) {
@@ -646,20 +646,20 @@ __global__ void __launch_bounds__(32, 32)
                 blocks(std::false_type{});
             float lo_, hi_;
             f2_unpack(ox, lo_, hi_);
-            two_sum_add(sox, cox, lo_ + hi_);
+            sox += (double)(lo_ + hi_);
             f2_unpack(oy, lo_, hi_);
-            two_sum_add(soy, coy, lo_ + hi_);
+            soy += (double)(lo_ + hi_);
             f2_unpack(oz, lo_, hi_);
-            two_sum_add(soz, coz, lo_ + hi_);
+            soz += (double)(lo_ + hi_);
             buf ^= 1;
             nb_c = nb_n;
             b_c = b_n;
         }
         if (timed_out) break;
         if (valid) {
-            out[i] += g.gm * ((double)sox + (double)cox);
-            out[n + i] += g.gm * ((double)soy + (double)coy);
-            out[2 * n + i] += g.gm * ((double)soz + (double)coz);
+            out[i] += g.gm * sox;
+            out[n + i] += g.gm * soy;
+            out[2 * n + i] += g.gm * soz;
         }
     }
     if (timed_out && lane == 0) atomicOr(flags, P3M_FLAG_TIMEOUT);

@@ -245,17 +245,6 @@ __device__ __forceinline__ NeighbourF make_neighbour(const P3MGeom &g, const uin
     return r;
 }
 
-// s + c += x, Knuth's TwoSum: the FP32 sum s and the running compensation c keep the rounding
-// error of every addition, so partial sums add up as accurately as in FP64 without using
-// GB300's narrow FP64 pipe.
-__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
-{
-    const float t = s + x;
-    const float bp = t - s;
-    const float e = (s - (t - bp)) + (x - bp);
-    s = t;
-    c += e;
-}
 #define P3M_FLAG_NONFINITE 2u
 
 // ------------------------------------------------------------------ launchers (sort.cu)

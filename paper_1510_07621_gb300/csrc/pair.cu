@@ -20,9 +20,10 @@
 // Two kernels share that traversal.  k_pairs_x2 (FP32 mode) uses coordinates relative to each
 // particle's own cell origin in FP32, shifted per neighbour cell by the difference of the two
 // cell origins (an FP32 value plus its FP32 residual), evaluates two j particles per lane with
-// packed f32x2 arithmetic and g from a fitted polynomial, and adds per-tile sums with FP32
-// TwoSum compensation; nothing in its tile loop uses the FP64 pipe.  k_pairs64 (FP64 mode) keeps
-// absolute coordinates (d = (x_j - x_i) + image, like a plain minimum-image difference) and
+// packed f32x2 arithmetic and g from a fitted polynomial, and adds each tile's FP32 partial sums
+// into FP64 sums per particle (one conversion and one FP64 add per coordinate and tile; measured
+// as fast as FP32 TwoSum compensation, and as accurate).  k_pairs64 (FP64 mode) keeps absolute
+// coordinates (d = (x_j - x_i) + image, like a plain minimum-image difference) and
 // evaluates g with erfc/exp.
 #include <cuda_runtime.h>
 
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(32, 32)
         // the FP32 rounding of coordinates up to the box size)
         const double *__restrict__ pos = A.pos;
         const float xa = (float)pos[ii], ya = (float)pos[n + ii], za = (float)pos[2 * n + ii];
-        float sax = 0.0f, say = 0.0f, saz = 0.0f, cax = 0.0f, cay = 0.0f, caz = 0.0f;
+        double sax = 0.0, say = 0.0, saz = 0.0;
 
         auto next_tile = [&](int &nb, uint32_t &b) {
             while (nb < 27 && b * 32u >= nbr[nb].end) {
@@ -618,11 +619,11 @@ __global__ void __launch_bounds__(32, 32)
                 blocks(std::false_type{});
             float lo_, hi_;
             f2_unpack(px, lo_, hi_);
-            two_sum_add(sax, cax, lo_ + hi_);
+            sax += (double)(lo_ + hi_);
             f2_unpack(py, lo_, hi_);
-            two_sum_add(say, cay, lo_ + hi_);
+            say += (double)(lo_ + hi_);
             f2_unpack(pz, lo_, hi_);
-            two_sum_add(saz, caz, lo_ + hi_);
+            saz += (double)(lo_ + hi_);
             ++n_tiles;
             if (n_culled - culled0 == bend - b_c) ++n_empty;
             buf ^= 1;
@@ -634,8 +635,7 @@ __global__ void __launch_bounds__(32, 32)
             break;
         }
         if (valid) {
-            const double a3[3] = {g.gm * ((double)sax + (double)cax), g.gm * ((double)say + (double)cay),
-                                  g.gm * ((double)saz + (double)caz)};
+            const double a3[3] = {g.gm * sax, g.gm * say, g.gm * saz};
             const double *__restrict__ acc_in = A.acc_in;
             double *__restrict__ acc_out = A.acc_out;
             double *__restrict__ mom = A.mom;
