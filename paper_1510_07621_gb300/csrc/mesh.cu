@@ -74,13 +74,19 @@ __device__ __forceinline__ unsigned long long to_fixed<double>(double w, double 
 // Fixed-size chunks of the sorted particles (CTA b takes slots [b*512, (b+1)*512)), so that a
 // dense cell is spread over many CTAs.  The chunk's CIC nodes are accumulated in a shared-memory
 // tile spanning the chunk's node bounding box (found by a block reduction); the tile is then
-// added to the mesh with one global atomic per non-zero node.  That pays for dense chunks (more
-// particles than box nodes); a sparse chunk, whose box holds more nodes than it has particles,
-// adds its 8 weights per particle straight to the mesh, as does a chunk whose box exceeds the
-// tile capacity (e.g. one that straddles the periodic boundary).  All sums are 64-bit
-// fixed-point integers (to_fixed); with them, tiles for every chunk that fits made the deposit
-// 28 % slower on the evolved 128^3 state and 42 % slower at 256^3 (64-bit shared-memory atomics
-// cost more than the global reductions they save).
+// added to the mesh with one global atomic per non-zero node.  A chunk whose box exceeds the
+// tile capacity (e.g. one that straddles the periodic boundary) adds its 8 weights per particle
+// straight to the mesh.  All sums are 64-bit fixed-point integers (to_fixed).  64-bit
+// shared-memory atomics are slow, so in the FP32 mode every 2^-32 fixed-point addend v is split
+// into v >> 16 and v & 0xFFFF, added by 32-bit atomics to two tiles (high and low); the tile
+// node is then (high << 16) + low, exactly the 64-bit sum.  Neither tile can overflow: a node
+// takes at most one addend per particle of the chunk (runs of equal-base lanes are summed first),
+// at most 512 of weight at most 1 + 2^-20 each, so high < 2^26 and low < 2^25.  Against 64-bit
+// tiles for dense chunks only (sparse chunks through global atomics): evolved 128^3 0.151 ->
+// 0.060 ms, synthetic clustered 0.157 -> 0.066 ms, 256^3 near-uniform 0.478 -> 0.335 ms (a
+// 32-bit variant of the same tiles is what made the difference; 64-bit tiles for every chunk
+// were slower than the global atomics, 0.187 and 0.594 ms).  The FP64 mode (2^-S with S up to
+// 62 - bit length of N) keeps 64-bit tiles, for dense chunks only.
 constexpr int kDepChunk = 512;
 constexpr int kDepTileMax = 4096;  // nodes
 
@@ -95,6 +101,8 @@ __global__ void __launch_bounds__(256)
     const int csh = 3 * g.sub_bits;
     __shared__ unsigned long long tile[kDepTileMax];
     __shared__ int s_lo[3][8], s_hi[3][8];
+    constexpr bool k32 = sizeof(T) == 4;  // split 32-bit tiles (FP32 mode)
+    unsigned int *const tile_hi = (unsigned int *)tile, *const tile_lo = tile_hi + kDepTileMax;
     const int M = g.mesh;
     const int64_t n = g.n;
     const int64_t base = (int64_t)blockIdx.x * kDepChunk;
@@ -155,8 +163,13 @@ __global__ void __launch_bounds__(256)
         bdim[d] = b - a + 1;
     }
     const long long vol = (long long)bdim[0] * bdim[1] * bdim[2];
-    if (vol <= kDepTileMax && vol <= kDepChunk) {
-        for (int t = threadIdx.x; t < vol; t += 256) tile[t] = 0ull;
+    if (vol <= kDepTileMax && (k32 || vol <= kDepChunk)) {
+        for (int t = threadIdx.x; t < vol; t += 256) {
+            if (k32)
+                tile_hi[t] = tile_lo[t] = 0u;
+            else
+                tile[t] = 0ull;
+        }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < per; ++r) {
@@ -196,20 +209,36 @@ __global__ void __launch_bounds__(256)
                 for (int b = 0; b < 2; ++b) {
                     const long long t = ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz;
                     if (!p3m_in_bounds(t >= 0 && t + 1 < vol, g.flags)) continue;
-                    unsigned long long *row = tile + t;
-                    atomicAdd(row, to_fixed(w[(a << 2) | (b << 1)], scale));
-                    atomicAdd(row + 1, to_fixed(w[(a << 2) | (b << 1) | 1], scale));
+                    const unsigned long long v0 = to_fixed(w[(a << 2) | (b << 1)], scale);
+                    const unsigned long long v1 = to_fixed(w[(a << 2) | (b << 1) | 1], scale);
+                    if (k32) {
+                        atomicAdd(tile_hi + t, (unsigned int)(v0 >> 16));
+                        atomicAdd(tile_lo + t, (unsigned int)(v0 & 0xFFFFu));
+                        atomicAdd(tile_hi + t + 1, (unsigned int)(v1 >> 16));
+                        atomicAdd(tile_lo + t + 1, (unsigned int)(v1 & 0xFFFFu));
+                    } else {
+                        atomicAdd(tile + t, v0);
+                        atomicAdd(tile + t + 1, v1);
+                    }
                 }
         }
         __syncthreads();
+        // t -> (lx, ly, lz) by FP32 reciprocals: for t, bdim < 2^12 the rounded quotient
+        // (t + 1/2) / bdim is off by far less than its distance 1/(2 bdim) to an integer.  Node
+        // indices lie in [-1, M + 1], so one conditional add or subtract wraps them.
+        const float inv_z = 1.0f / (float)bdim[2], inv_y = 1.0f / (float)bdim[1];
         for (int t = threadIdx.x; t < vol; t += 256) {
-            const unsigned long long v = tile[t];
-            if (v != 0ull) {
-                const int lz = t % bdim[2], ly = (t / bdim[2]) % bdim[1], lx = t / (bdim[2] * bdim[1]);
-                const size_t node = ((size_t)wrap_index(blo[0] + lx, M) * M + wrap_index(blo[1] + ly, M)) * M +
-                                    wrap_index(blo[2] + lz, M);
-                if (p3m_in_bounds(node < (size_t)M * M * M, g.flags)) atomicAdd(fix + node, v);
-            }
+            const unsigned long long v =
+                k32 ? ((unsigned long long)tile_hi[t] << 16) + tile_lo[t] : tile[t];
+            if (v == 0ull) continue;
+            const int row = (int)(((float)t + 0.5f) * inv_z), lz = t - row * bdim[2];
+            const int lx = (int)(((float)row + 0.5f) * inv_y), ly = row - lx * bdim[1];
+            int wx = blo[0] + lx, wy = blo[1] + ly, wz = blo[2] + lz;
+            wx += wx < 0 ? M : (wx >= M ? -M : 0);
+            wy += wy < 0 ? M : (wy >= M ? -M : 0);
+            wz += wz < 0 ? M : (wz >= M ? -M : 0);
+            const size_t node = ((size_t)wx * M + wy) * M + wz;
+            if (p3m_in_bounds(node < (size_t)M * M * M, g.flags)) atomicAdd(fix + node, v);
         }
     } else {
 #pragma unroll
@@ -294,9 +323,163 @@ __global__ void __launch_bounds__(256)
 }
 
 // CIC interpolation of the three mesh accelerations at the particles.  FP32 mode: the stencil
-// comes from the cell-relative coordinates (right after the permute); FP64 mode: from the FP64
-// positions.  (Writing the three C2R outputs interleaved per node, so that a node is one 16-byte
-// load, made this gather 34 % faster at 256^3 but the strided C2R 2.3x slower: not kept.)
+// comes from the cell-relative coordinates (right after the permute).  When the three force
+// meshes do not fit in L2, k_gather_f32_staged takes a chunk of 512 consecutive sorted
+// particles per CTA: it finds the chunk's node bounding box (block reduction), copies that box
+// of the three meshes into shared memory, and interpolates from there.  24 scattered global
+// loads per particle (8 nodes x 3 meshes) kept the L1 request pipeline saturated at large
+// meshes (256^3: 0.51 -> 0.38 ms, 512^3: 4.6 -> 3.3 ms).  With the meshes in L2, the direct
+// loads of k_gather_f32 were faster (evolved 128^3: 0.047 against 0.051 ms); a chunk whose box
+// exceeds the tile (one that straddles the periodic boundary or spans sparse cells) reads the
+// meshes directly too.  Every path adds the same products in the same order, so the result
+// does not depend on the path.  FP64 mode: the stencil from the FP64 positions.  (Writing the
+// three C2R outputs interleaved per node, so that a node is one 16-byte load, made a direct
+// gather 34 % faster at 256^3 but the strided C2R 2.3x slower: not kept.)
+constexpr int kGatherChunk = 512;
+constexpr int kGatherTileMax = 2048;  // nodes (three FP32 meshes: 24 KB)
+
+// the chunk's node bounding box (origin blo, extent bdim) from the threads' stencil bounds
+__device__ __forceinline__ void chunk_box(int lo[3], int hi[3], int blo[3], int bdim[3])
+{
+    __shared__ int s_lo[3][8], s_hi[3][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+        if (lane == 0) {
+            s_lo[d][warp] = lo[d];
+            s_hi[d][warp] = hi[d];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int a = INT_MAX, b = INT_MIN;
+        for (int w = 0; w < 8; ++w) {
+            a = min(a, s_lo[d][w]);
+            b = max(b, s_hi[d][w]);
+        }
+        blo[d] = a;
+        bdim[d] = b - a + 1;  // (no active particle: a > b, bdim <= 0)
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_gather_f32_staged(const float4 *__restrict__ rel, const uint32_t *__restrict__ keys, P3MGeom g,
+                        const float *__restrict__ fxm, const float *__restrict__ fym,
+                        const float *__restrict__ fzm, double *__restrict__ acc)
+{
+    __shared__ float tile[3][kGatherTileMax];
+    const int M = g.mesh;
+    const int64_t n = g.n;
+    const float inv_h_f = (float)g.inv_h, inv_nc = 1.0f / (float)g.n_c;
+    const int csh = 3 * g.sub_bits;
+    const int64_t base = (int64_t)blockIdx.x * kGatherChunk;
+    constexpr int per = kGatherChunk / 256;
+    int i0[per][3];
+    float f[per][3];
+    bool act[per];
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+#pragma unroll
+    for (int r = 0; r < per; ++r) {
+        const int64_t k = base + r * 256 + threadIdx.x;
+        act[r] = k < n;
+        int ii[3] = {0, 0, 0};
+        float ff[3] = {0.0f, 0.0f, 0.0f};
+        if (act[r]) cic_stencil_rel(rel[k], keys[k] >> csh, g, inv_h_f, inv_nc, ii, ff);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            i0[r][d] = ii[d];
+            f[r][d] = ff[d];
+            if (act[r]) {
+                lo[d] = min(lo[d], ii[d]);
+                hi[d] = max(hi[d], ii[d] + 1);
+            }
+        }
+    }
+    int blo[3], bdim[3];
+    chunk_box(lo, hi, blo, bdim);
+    const long long vol = (long long)bdim[0] * bdim[1] * bdim[2];
+    if (bdim[0] > 0 && vol <= kGatherTileMax) {
+        // t -> (lx, ly, lz) by FP32 reciprocals: for t, bdim < 2^11 the rounded quotient
+        // (t + 1/2) / bdim is off by far less than its distance 1/(2 bdim) to an integer.  Node
+        // indices lie in [-1, M + 1], so one conditional add or subtract wraps them.
+        const float inv_z = 1.0f / (float)bdim[2], inv_y = 1.0f / (float)bdim[1];
+        for (int t = threadIdx.x; t < vol; t += 256) {
+            const int row = (int)(((float)t + 0.5f) * inv_z), lz = t - row * bdim[2];
+            const int lx = (int)(((float)row + 0.5f) * inv_y), ly = row - lx * bdim[1];
+            int wx = blo[0] + lx, wy = blo[1] + ly, wz = blo[2] + lz;
+            wx += wx < 0 ? M : (wx >= M ? -M : 0);
+            wy += wy < 0 ? M : (wy >= M ? -M : 0);
+            wz += wz < 0 ? M : (wz >= M ? -M : 0);
+            const size_t node = ((size_t)wx * M + wy) * M + wz;
+            const bool ok = p3m_in_bounds(node < (size_t)M * M * M, g.flags);
+            tile[0][t] = ok ? __ldg(fxm + node) : 0.0f;
+            tile[1][t] = ok ? __ldg(fym + node) : 0.0f;
+            tile[2][t] = ok ? __ldg(fzm + node) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < per; ++r) {
+            if (!act[r]) continue;
+            const int64_t k = base + r * 256 + threadIdx.x;
+            const float wx[2] = {1.0f - f[r][0], f[r][0]}, wy[2] = {1.0f - f[r][1], f[r][1]},
+                        wz[2] = {1.0f - f[r][2], f[r][2]};
+            const int lx = i0[r][0] - blo[0], ly = i0[r][1] - blo[1], lz = i0[r][2] - blo[2];
+            float ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const float w = wx[a] * wy[b] * wz[c];
+                        const int t = ((lx + a) * bdim[1] + (ly + b)) * bdim[2] + lz + c;
+                        if (!p3m_in_bounds(t >= 0 && t < vol, g.flags)) continue;
+                        ax += w * tile[0][t];
+                        ay += w * tile[1][t];
+                        az += w * tile[2][t];
+                    }
+            acc[k] = (double)ax;
+            acc[n + k] = (double)ay;
+            acc[2 * n + k] = (double)az;
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < per; ++r) {
+        if (!act[r]) continue;
+        const int64_t k = base + r * 256 + threadIdx.x;
+        const float wx[2] = {1.0f - f[r][0], f[r][0]}, wy[2] = {1.0f - f[r][1], f[r][1]},
+                    wz[2] = {1.0f - f[r][2], f[r][2]};
+        const int jx[2] = {wrap_index(i0[r][0], M), wrap_index(i0[r][0] + 1, M)};
+        const int jy[2] = {wrap_index(i0[r][1], M), wrap_index(i0[r][1] + 1, M)};
+        const int jz[2] = {wrap_index(i0[r][2], M), wrap_index(i0[r][2] + 1, M)};
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float w = wx[a] * wy[b] * wz[c];
+                    const size_t node = ((size_t)jx[a] * M + jy[b]) * M + jz[c];
+                    if (!p3m_in_bounds(node < (size_t)M * M * M, g.flags)) continue;
+                    ax += w * __ldg(fxm + node);
+                    ay += w * __ldg(fym + node);
+                    az += w * __ldg(fzm + node);
+                }
+        acc[k] = (double)ax;
+        acc[n + k] = (double)ay;
+        acc[2 * n + k] = (double)az;
+    }
+}
+
+// The direct FP32 gather (meshes in L2): one particle per thread, grid-stride.
 __global__ void __launch_bounds__(256)
     k_gather_f32(const float4 *__restrict__ rel, const uint32_t *__restrict__ keys, P3MGeom g,
                  const float *__restrict__ fxm, const float *__restrict__ fym,
@@ -564,8 +747,14 @@ cudaError_t launch_gather(p3m_ctx *c, double *acc_out)
     c->launches += 1;
     if (c->precision == P3M_PREC_MIXED) {
         const float *f = (const float *)c->frc;
-        k_gather_f32<<<grid, 256, 0, c->stream>>>((const float4 *)c->rel, c->keys, c->g, f, f + M3,
-                                                  f + 2 * M3, acc_out);
+        if (3 * sizeof(float) * M3 > (size_t)c->l2_bytes) {  // the meshes do not fit in L2
+            const unsigned chunks = (unsigned)((c->g.n + kGatherChunk - 1) / kGatherChunk);
+            k_gather_f32_staged<<<chunks, 256, 0, c->stream>>>((const float4 *)c->rel, c->keys, c->g, f,
+                                                               f + M3, f + 2 * M3, acc_out);
+        } else {
+            k_gather_f32<<<grid, 256, 0, c->stream>>>((const float4 *)c->rel, c->keys, c->g, f, f + M3,
+                                                      f + 2 * M3, acc_out);
+        }
     } else {
         const double *f = (const double *)c->frc;
         k_gather_f64<<<grid, 256, 0, c->stream>>>(c->pos, c->g, f, f + M3, f + 2 * M3, acc_out);

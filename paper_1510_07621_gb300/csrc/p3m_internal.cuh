@@ -61,6 +61,7 @@ struct p3m_ctx {
     double a;
     cudaStream_t stream;
     int num_sms;
+    int l2_bytes;  // L2 cache size of the device
 
     // particle state in sorted order, SoA [3][n]
     double *pos, *mom, *acc, *acc_lr;
