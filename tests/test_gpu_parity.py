@@ -151,6 +151,26 @@ def test_density_mesh(P3M, precision):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_density_mesh_exact_on_dyadic_positions(P3M, precision):
+    """Positions on a quarter-node grid of a 48^3 mesh (box 48: node spacing 1, chaining cells of
+    6 nodes) make every CIC weight a dyadic fraction that FP32 holds exactly, and N = M^3 / 8
+    makes the mean 1/8.  The fixed-point deposit (split 32-bit shared tiles, run sums of equal
+    base nodes, global atomics for chunks that straddle the periodic boundary) must then give the
+    definition's mesh exactly.  Clumps of 8 coincident particles make runs of equal base node."""
+    M = 48
+    u = S.uniform01(4242, 3 * 1728).reshape(3, 1728)
+    pos = np.repeat(np.floor(u * 4 * M) / 4, 8, axis=1)  # 1728 clumps x 8 = 48^3 / 8
+    n = pos.shape[1]
+    with P3M(float(M), n, M, precision=precision) as sim:
+        assert sim.geometry()["n_c"] == 8
+        sim.set_particles(pos, np.zeros_like(pos), a=1.0)
+        sim.forces(1.0)
+        rho = sim.get_mesh(0).astype(np.float64)
+    ref = O.cic_deposit(pos, O.Params(float(M), n, M)) - n / M ** 3
+    assert np.array_equal(rho, ref), np.max(np.abs(rho - ref))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("case", ["eds32", "clustered48", "random5003", "tiny3", "nc3",
                                   "coincident"])
 def test_force_parts_match_oracle(P3M, case, precision):
