@@ -150,6 +150,20 @@ def test_density_mesh(P3M, precision):
     assert np.max(np.abs(rho - ref)) <= tol * np.max(np.abs(ref))
 
 
+def test_staged_gather_matches_oracle(P3M):
+    """A 256^3 mesh: the three FP32 force meshes (201 MB) exceed L2, so the mixed-mode gather
+    copies each 512-particle chunk's node box into shared memory; the clustered 64^3 particles
+    give compact chunks (the staged path) and sparse ones whose boxes exceed the tile (direct
+    loads).  The mesh force must match the oracle's (CIC gather of the same mesh force)."""
+    pos, mom = S.clustered(64, 256.0, 4002)
+    n = pos.shape[1]
+    with P3M(256.0, n, 256) as sim:
+        sim.set_particles(pos, mom, a=1.0)
+        lr, _ = sim.forces_split()
+    ref = O.pm_accel(O.wrap(pos, 256.0), O.Params(256.0, n, 256, softening=0.02))
+    assert rel_rms(lr, ref) <= TOL["mixed"], rel_rms(lr, ref)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_density_mesh_exact_on_dyadic_positions(P3M, precision):
     """Positions on a quarter-node grid of a 48^3 mesh (box 48: node spacing 1, chaining cells of
