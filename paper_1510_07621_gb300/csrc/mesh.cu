@@ -81,12 +81,12 @@ __device__ __forceinline__ unsigned long long to_fixed<double>(double w, double 
 // into v >> 16 and v & 0xFFFF, added by 32-bit atomics to two tiles (high and low); the tile
 // node is then (high << 16) + low, exactly the 64-bit sum.  Neither tile can overflow: a node
 // takes at most one addend per particle of the chunk (runs of equal-base lanes are summed first),
-// at most 512 of weight at most 1 + 2^-20 each, so high < 2^26 and low < 2^25.  Against 64-bit
-// tiles for dense chunks only (sparse chunks through global atomics): evolved 128^3 0.151 ->
-// 0.060 ms, synthetic clustered 0.157 -> 0.066 ms, 256^3 near-uniform 0.478 -> 0.335 ms (a
-// 32-bit variant of the same tiles is what made the difference; 64-bit tiles for every chunk
-// were slower than the global atomics, 0.187 and 0.594 ms).  The FP64 mode (2^-S with S up to
-// 62 - bit length of N) keeps 64-bit tiles, for dense chunks only.
+// at most 512 of weight at most 1 + 2^-20 each, so high < 2^26 and low < 2^25.  With the split
+// tiles every chunk that fits uses its tile; against 64-bit tiles for dense chunks only (sparse
+// chunks through global atomics): evolved 128^3 0.151 -> 0.079 ms, synthetic clustered 0.155 ->
+// 0.083 ms, 256^3 near-uniform 0.480 -> 0.417 ms, 512^3 3.73 -> 3.13 ms (64-bit tiles for every
+// chunk were slower than the global atomics: 0.187, 0.190 and 0.594 ms).  The FP64 mode (2^-S
+// with S up to 62 - bit length of N) keeps 64-bit tiles, for dense chunks only.
 constexpr int kDepChunk = 512;
 constexpr int kDepTileMax = 4096;  // nodes
 
