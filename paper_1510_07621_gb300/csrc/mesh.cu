@@ -99,10 +99,14 @@ __global__ void __launch_bounds__(256)
     // rel != nullptr (FP32 mode, sorted state fresh): FP32 stencils from rel and the keys' cells
     const float inv_h_f = (float)g.inv_h, inv_nc = 1.0f / (float)g.n_c;
     const int csh = 3 * g.sub_bits;
-    __shared__ unsigned long long tile[kDepTileMax];
+    __shared__ union {
+        unsigned long long u64[kDepTileMax];    // FP64 mode: 64-bit tile
+        unsigned int u32[2][kDepTileMax];       // FP32 mode: high and low tiles
+    } tiles;
+    unsigned long long *const tile = tiles.u64;
     __shared__ int s_lo[3][8], s_hi[3][8];
     constexpr bool k32 = sizeof(T) == 4;  // split 32-bit tiles (FP32 mode)
-    unsigned int *const tile_hi = (unsigned int *)tile, *const tile_lo = tile_hi + kDepTileMax;
+    unsigned int *const tile_hi = tiles.u32[0], *const tile_lo = tiles.u32[1];
     const int M = g.mesh;
     const int64_t n = g.n;
     const int64_t base = (int64_t)blockIdx.x * kDepChunk;
