@@ -41,11 +41,15 @@ import p3m_synth as S  # noqa: E402
 METRIC = "P3M particle-updates/s"
 UNIT = "particle-updates/s"
 # algorithmic FP32 flops per accepted pair of the short-range sum: the FP32 arithmetic of the
-# accepted-pair instruction sequence, FMA = 2: d 3 FADD; r^2 FMUL + 2 FFMA; r = r^2 rsqrt(r^2)
-# FMUL; r^3 FMUL; tau FFMA; Q(tau) 10 FFMA; g = 1 + r^3 Q FFMA; r^2 + eps^2 FADD;
-# g (r^2+eps^2)^-3/2 3 FMUL; a += f d 3 FFMA  ->  17 FFMA + 10 FADD/FMUL = 44 flops
-# (the two rsqrt run on the MUFU pipe and are not counted)
-FLOPS_PER_PAIR = 44
+# FP32 kernel's accepted-pair sequence, FMA = 2: d 3 FADD; r^2 3 FFMA; r^2 + eps^2 FADD;
+# s^3 = rsqrt * rcp FMUL; r^3 = r^2 sqrt(r^2) FMUL; tau FFMA; the degree-8 Horner chain 8 FFMA;
+# g = 1 + r^3 p FFMA; f = g s^3 FMUL; a += f d 3 FFMA  ->  16 FFMA + 7 FADD/FMUL = 39 flops
+# (sqrt, rsqrt and rcp run on the MUFU pipe and are not counted)
+FLOPS_PER_PAIR = 39
+# the same for the FP64 kernel: d 6 DADD (difference plus image); r^2 DMUL + 2 DFMA; r^2 + eps^2
+# DADD; r^3 = r^2 (r^2 rsqrt(r^2)) 2 DMUL; tau DFMA; the degree-18 Horner chain 18 DFMA;
+# g DFMA; s^3 and g s^3 3 DMUL; a += f d 3 DFMA  ->  25 DFMA + 13 DADD/DMUL = 63 flops
+FLOPS_PER_PAIR_FP64 = 63
 WORKLOAD = dict(n_p=128, mesh=128, box=200.0, r_s_cells=1.25, cutoff=4.5, softening=0.02,
                 a_begin=0.02, a_end=1.0, setup_steps=64, seed=1512)
 WORKLOAD_NAME = ("clustered_128: 128^3 particles, 128^3 mesh, box 200 Mpc/h, r_s 1.25 cells, "
@@ -411,9 +415,10 @@ def run_ours(args, rank, world, local_rank, dist):
         out["fp64_gpu"] = {"value": n / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                            "steps": args.fp64_steps,
                            "mixed_vs_fp64_force_rel_rms": rms,
-                           "pair_tflops": pairs64 * FLOPS_PER_PAIR / (ms64 / 1e3) / 1e12,
+                           "pair_tflops": pairs64 * FLOPS_PER_PAIR_FP64 / (ms64 / 1e3) / 1e12,
+                           "flops_per_pair": FLOPS_PER_PAIR_FP64,
                            "fp64_fma_peak_measured": fma64,
-                           "pair_frac_of_fp64_peak": pairs64 * FLOPS_PER_PAIR / (ms64 / 1e3) / 1e12 / fma64,
+                           "pair_frac_of_fp64_peak": pairs64 * FLOPS_PER_PAIR_FP64 / (ms64 / 1e3) / 1e12 / fma64,
                            "speedup_mixed_over_fp64": value / world / (n / (ms64 / 1e3))}
 
     # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1 only), on the
