@@ -51,6 +51,24 @@ def test_debug_build_passes_its_checks_and_matches_release(libs, precision):
         assert np.array_equal(x, y)
 
 
+def test_debug_build_staged_gather(libs):
+    """A 256^3 mesh, whose three FP32 force meshes exceed L2, takes the staged gather (chunk node
+    boxes in shared memory, tile indices from FP32 reciprocals) and the split-tile deposit with
+    sparse and dense chunks: every tile index stays in bounds, and the results equal the
+    release build's."""
+    torch, _lib, rel, dbg = libs
+    import paper_1510_07621_gb300 as m
+    pos, mom = S.clustered(64, 256.0, 4002)
+    out = []
+    for lib in (dbg, rel):
+        with m.P3M(256.0, pos.shape[1], 256, lib=lib) as sim:
+            sim.set_particles(pos, mom, a=1.0)
+            out.append(sim.forces_split()[0])
+            out.append(sim.get_mesh(0))
+            assert lib.p3m_debug_check(sim._ctx) == 0, lib.p3m_last_error(sim._ctx).decode()
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
+
+
 def test_debug_build_ensemble_with_graphs(libs):
     torch, _lib, rel, dbg = libs
     import paper_1510_07621_gb300 as m
