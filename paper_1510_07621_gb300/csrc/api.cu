@@ -577,6 +577,7 @@ extern "C" int p3m_init(p3m_ctx **out, double box, int64_t n, int mesh, double r
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, dev);
+        if (e == cudaSuccess) e = mesh_set_attributes();
         if (e != cudaSuccess) {
             rc = fail(nullptr, P3M_ECUDA, "p3m_init: no CUDA device: %s", cudaGetErrorString(e));
             break;

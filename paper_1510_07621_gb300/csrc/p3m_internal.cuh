@@ -268,6 +268,8 @@ cudaError_t launch_deposit(p3m_ctx *c, bool from_rel = false);
 cudaError_t launch_kspace(p3m_ctx *c);
 // Right after the permute: the FP32 mode reads the stencils from the sorted rel and keys.
 cudaError_t launch_gather(p3m_ctx *c, double *acc_out);
+// kernel attributes of the mesh kernels (shared-memory carveout), set once per process
+cudaError_t mesh_set_attributes();
 // Bins the spectrum in c->rho_k into acc[3 n_bins + 1] (see k_powspec).
 cudaError_t launch_powspec(p3m_ctx *c, const double *inv_w2, double radius, int n_bins, double *acc);
 
