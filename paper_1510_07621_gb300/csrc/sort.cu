@@ -475,7 +475,7 @@ __device__ __forceinline__ double4_16a rel_coords<double4_16a>(double x, double 
 }
 
 template <typename R4>
-__global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys,
+__global__ void __launch_bounds__(256, 6) k_permute(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ keys,
                           P3MGeom g, const double *__restrict__ pos,
                           const double *__restrict__ mom, const uint32_t *__restrict__ pid,
                           double *__restrict__ pos_out, double *__restrict__ mom_out,
@@ -484,7 +484,8 @@ __global__ void k_permute(const uint32_t *__restrict__ perm, const uint32_t *__r
                           const double *__restrict__ origin)
 {
     // one warp per 32-slot block of the sorted order; the warp also writes the block's
-    // bounding box (FP32, absolute coordinates, rounded outwards by the callers' margins)
+    // bounding box (FP32, absolute coordinates, rounded outwards by the callers' margins).
+    // Six CTAs per SM (40 registers): the permute phase 0.644 -> 0.619 ms at 256^3 against five.
     const int64_t n = g.n;
     const int64_t nblocks = (n + 31) >> 5;
     const int lane = threadIdx.x & 31;
