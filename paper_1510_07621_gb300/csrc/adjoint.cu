@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(32, 32)
         if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
         // x_i in the current neighbour cell's frame, set when the tile walk enters the cell
         int nb_frame = -1;
-        f2 xs2 = 0, ys2 = 0, zs2 = 0;
+        f2 xs2 = make_float2(0.0f, 0.0f), ys2 = xs2, zs2 = xs2;
         float cxs = 0.0f, cys = 0.0f, czs = 0.0f;
         while (nb_c < 27) {
             const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(32, 32)
                 cys = ya - q.imy;
                 czs = za - q.imz;
             }
-            f2 ox = 0, oy = 0, oz = 0;
+            f2 ox = make_float2(0.0f, 0.0f), oy = ox, oz = ox;
 
             // pair (j, j+1) from packed coordinates (x, y, z) and v (u, v, w); lo/hi: which
             // halves take part; test: r < r_c; own: the work item's own cell (r^2 > kVjpTiny test)

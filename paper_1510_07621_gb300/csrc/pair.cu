@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(32, 32)
         if (nb_c < 27 && lane == 0) issue(nb_c, b_c, 0);
         // x_i in the current neighbour cell's frame, set when the tile walk enters the cell
         int nb_frame = -1;
-        f2 xs2 = 0, ys2 = 0, zs2 = 0;
+        f2 xs2 = make_float2(0.0f, 0.0f), ys2 = xs2, zs2 = xs2;
         float cxs = 0.0f, cys = 0.0f, czs = 0.0f;
         while (nb_c < 27) {
             const uint32_t nstart = nbr[nb_c].start, nend = nbr[nb_c].end;
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(32, 32)
                 cys = ya - q.imy;
                 czs = za - q.imz;
             }
-            f2 px = 0, py = 0, pz = 0;  // bit pattern 0 = (+0.0f, +0.0f)
+            f2 px = make_float2(0.0f, 0.0f), py = px, pz = px;
             const uint32_t culled0 = n_culled;
 
             // Pair counts: a pair is counted when kTiny < r^2 < r_c^2.  r^2 = kTiny (all three
