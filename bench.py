@@ -426,7 +426,7 @@ def run_ours(args, rank, world, local_rank, dist):
                            "pair_frac_of_fp64_peak": pairs64 * FLOPS_PER_PAIR_FP64 / (ms64 / 1e3) / 1e12 / fma64,
                            "speedup_mixed_over_fp64": value / world / (n / (ms64 / 1e3))}
 
-    # ---- CPU baseline: the oracle on this box's host cores (rank 0, N = 1 only), on the
+    # ---- CPU baseline: the oracle on this machine's host cores (rank 0, N = 1 only), on the
     # synthetic clustered a = 1 stand-in snapshot: no oracle input comes from the GPU path.  The
     # GPU path is timed on the same snapshot too, so that the two rates compare like work.
     if rank == 0 and world == 1 and args.cpu_stride > 0:
